@@ -1,0 +1,305 @@
+/*
+ * FP64 reference ("oracle") of the B-mode reconstruction path: delay-and-sum
+ * beamforming (STAI and PWI), analytic signal, magnitude, log compression
+ * with dynamic-range clipping.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, loads or
+ * calls this file; it exists so that tests, the smoke check and the CPU
+ * baseline leg of the benchmark have an independent, obviously correct
+ * answer to compare the CUDA path against.  It shares no code, header,
+ * table or constant with the CUDA sources.
+ *
+ * Everything is plain single-threaded C in double precision, written as the
+ * direct definition of each step, in the order the paper's pipeline
+ * (Fig. 2) applies them: Beamforming -> Analytic Signal -> Absolute Value ->
+ * Dynamic Adjustment.  The paper names the steps (Sec. II-B: DAS beamformer
+ * with STAI and PWI; envelope detection; dynamic adjustment; Hilbert
+ * transform built on the FFT) but prints none of their formulas, so the
+ * formulas below are the standard textbook definitions; each reading the
+ * paper leaves open is stated at the function that makes it.
+ *
+ * Geometry: a linear array on the line z = 0 with element e at
+ * x_e = (e - (E-1)/2) * pitch; pixel (iz, ix) sits at
+ * x = x_min + ix (x_max - x_min)/(nx - 1), z = z_min + iz (z_max - z_min)/(nz - 1)
+ * (a grid of 1 along an axis sits at the lower bound).  Images are
+ * [nz][nx], x fastest.  RF is [n_tx][n_rx][n_samples], samples fastest, the
+ * paper's [acquisitions, channels, samples] layout (Sec. III).
+ */
+#include <math.h>
+#include <stddef.h>
+#include <stdint.h>
+#include <string.h>
+#include <stdlib.h>
+
+#define OR_HANN 0
+#define OR_RECT 1
+#define OR_NONE 2
+
+typedef struct {
+    int32_t n_elements;
+    double pitch;          /* m */
+    double fs;             /* Hz */
+    double c;              /* m/s */
+    double f_number;
+    int32_t apod;          /* OR_HANN / OR_RECT / OR_NONE */
+    const double* elem_weight; /* [n_elements] or NULL (all ones) */
+} or_probe;
+
+typedef struct {
+    int32_t nz, nx;
+    double x_min, x_max, z_min, z_max; /* m, pixel centres, inclusive */
+} or_grid;
+
+/* Position of element e on the array (x, at z = 0). */
+double or_element_x(const or_probe* p, int32_t e)
+{
+    return ((double)e - 0.5 * (double)(p->n_elements - 1)) * p->pitch;
+}
+
+/* Lateral / axial position of a pixel index. */
+double or_pixel_x(const or_grid* g, int32_t ix)
+{
+    if (g->nx <= 1) return g->x_min;
+    return g->x_min + (double)ix * (g->x_max - g->x_min) / (double)(g->nx - 1);
+}
+
+double or_pixel_z(const or_grid* g, int32_t iz)
+{
+    if (g->nz <= 1) return g->z_min;
+    return g->z_min + (double)iz * (g->z_max - g->z_min) / (double)(g->nz - 1);
+}
+
+/*
+ * Apodization weight of element e for the pixel (x, z) (Sec. II-B DAS).
+ * Reading: dynamic receive aperture of half-width a = z / (2F), normalised
+ * offset u = (x_e - x) / a; Hann: 0.5 (1 + cos(pi u)) for |u| < 1, else 0;
+ * rect: 1 for |u| < 1, else 0; none: 1 everywhere.  A pixel with z <= 0 has
+ * no aperture (weight 0) unless the apodization is "none".  The optional
+ * per-element weight g_e multiplies the window.
+ */
+double or_apod(const or_probe* p, double x, double z, int32_t e)
+{
+    double g = p->elem_weight ? p->elem_weight[e] : 1.0;
+    if (p->apod == OR_NONE) return g;
+    double a = z / (2.0 * p->f_number);
+    if (!(a > 0.0)) return 0.0;
+    double u = (or_element_x(p, e) - x) / a;
+    if (!(fabs(u) < 1.0)) return 0.0;
+    if (p->apod == OR_RECT) return g;
+    return g * 0.5 * (1.0 + cos(M_PI * u));
+}
+
+/* One-way distance from element e to the pixel (x, z), m. */
+static double or_dist(const or_probe* p, double x, double z, int32_t e)
+{
+    double dx = x - or_element_x(p, e);
+    return sqrt(dx * dx + z * z);
+}
+
+/*
+ * STAI delay in samples (Sec. II-B, synthetic transmit aperture): element
+ * et fires at t = 0, element er records; sample 0 is taken at t_start.
+ * s = (|p - e_t| + |p - e_r|) fs / c - t_start fs.
+ */
+double or_delay_stai(const or_probe* p, double x, double z, int32_t et, int32_t er,
+                     double t_start)
+{
+    return (or_dist(p, x, z, et) + or_dist(p, x, z, er)) * p->fs / p->c - t_start * p->fs;
+}
+
+/*
+ * PWI delay in samples (Sec. II-B, plane-wave imaging): the plane wave of
+ * angle theta passes the origin at t = 0 and reaches (x, z) after
+ * (x sin theta + z cos theta) / c; the echo returns to element er.
+ * s = (x sin theta + z cos theta + |p - e_r|) fs / c - t_start fs.
+ */
+double or_delay_pwi(const or_probe* p, double x, double z, double theta, int32_t er,
+                    double t_start)
+{
+    return (x * sin(theta) + z * cos(theta) + or_dist(p, x, z, er)) * p->fs / p->c
+           - t_start * p->fs;
+}
+
+/*
+ * Linear interpolation of one RF trace at fractional sample s.
+ * Reading: i = floor(s), f = s - i; the value is (1-f) tr[i] + f tr[i+1]
+ * when 0 <= i and i + 1 <= ns - 1, and 0 otherwise (no echo recorded).
+ */
+double or_lerp(const double* tr, int32_t ns, double s)
+{
+    double fi = floor(s);
+    if (!(fi >= 0.0) || !(fi + 1.0 <= (double)(ns - 1))) return 0.0;
+    int64_t i = (int64_t)fi;
+    double f = s - fi;
+    return (1.0 - f) * tr[i] + f * tr[i + 1];
+}
+
+/*
+ * STAI delay-and-sum (Sec. II-B; Fig. 2 "Beamforming"):
+ *   b(p) = sum_t w(p, e_t) sum_r w(p, r) lerp(rf[t][r], s_stai(p, e_t, r)).
+ * Terms whose apodization weight is zero are outside the aperture and are not
+ * part of the sum.  Writes rows [row_begin, row_end) of out[nz][nx].
+ */
+int or_das_stai(const or_probe* p, const or_grid* g, int32_t n_tx, const int32_t* tx_elem,
+                int32_t n_rx, int32_t ns, double t_start, const double* rf,
+                int32_t row_begin, int32_t row_end, double* out)
+{
+    if (n_rx != p->n_elements) return 1;
+    for (int32_t iz = row_begin; iz < row_end; ++iz) {
+        double z = or_pixel_z(g, iz);
+        for (int32_t ix = 0; ix < g->nx; ++ix) {
+            double x = or_pixel_x(g, ix);
+            double acc = 0.0;
+            for (int32_t t = 0; t < n_tx; ++t) {
+                int32_t et = tx_elem ? tx_elem[t] : t;
+                double wt = or_apod(p, x, z, et);
+                if (wt == 0.0) continue;
+                double inner = 0.0;
+                for (int32_t r = 0; r < n_rx; ++r) {
+                    double wr = or_apod(p, x, z, r);
+                    if (wr == 0.0) continue;
+                    double s = or_delay_stai(p, x, z, et, r, t_start);
+                    const double* tr = rf + ((size_t)t * n_rx + r) * (size_t)ns;
+                    inner += wr * or_lerp(tr, ns, s);
+                }
+                acc += wt * inner;
+            }
+            out[(size_t)iz * g->nx + ix] = acc;
+        }
+    }
+    return 0;
+}
+
+/*
+ * PWI delay-and-sum with coherent compounding over angles (Sec. II-B):
+ *   b(p) = sum_k sum_r w(p, r) lerp(rf[k][r], s_pwi(p, theta_k, r)).
+ * Receive apodization only; every angle has transmit weight 1.
+ */
+int or_das_pwi(const or_probe* p, const or_grid* g, int32_t n_ang, const double* angles,
+               const double* t_starts, int32_t n_rx, int32_t ns, const double* rf,
+               int32_t row_begin, int32_t row_end, double* out)
+{
+    if (n_rx != p->n_elements) return 1;
+    for (int32_t iz = row_begin; iz < row_end; ++iz) {
+        double z = or_pixel_z(g, iz);
+        for (int32_t ix = 0; ix < g->nx; ++ix) {
+            double x = or_pixel_x(g, ix);
+            double acc = 0.0;
+            for (int32_t k = 0; k < n_ang; ++k) {
+                double t0 = t_starts ? t_starts[k] : 0.0;
+                for (int32_t r = 0; r < n_rx; ++r) {
+                    double wr = or_apod(p, x, z, r);
+                    if (wr == 0.0) continue;
+                    double s = or_delay_pwi(p, x, z, angles[k], r, t0);
+                    const double* tr = rf + ((size_t)k * n_rx + r) * (size_t)ns;
+                    acc += wr * or_lerp(tr, ns, s);
+                }
+            }
+            out[(size_t)iz * g->nx + ix] = acc;
+        }
+    }
+    return 0;
+}
+
+/*
+ * Direct O(N^2) discrete Fourier transform (textbook definition):
+ *   forward  X[k] = sum_n x[n] exp(-2 pi i k n / N)
+ *   inverse  x[n] = (1/N) sum_k X[k] exp(+2 pi i k n / N)
+ * The phase index k n is reduced mod N in integers before the angle is
+ * formed, so every twiddle is cos/sin of 2 pi m / N with m < N.
+ */
+void or_dft(const double* xr, const double* xi, int32_t n, int32_t inverse,
+            double* yr, double* yi)
+{
+    double sgn = inverse ? 1.0 : -1.0;
+    for (int32_t k = 0; k < n; ++k) {
+        double ar = 0.0, ai = 0.0;
+        for (int32_t j = 0; j < n; ++j) {
+            int64_t m = ((int64_t)k * j) % n;
+            double ang = 2.0 * M_PI * (double)m / (double)n;
+            double c = cos(ang), s = sgn * sin(ang);
+            double vr = xr[j], vi = xi ? xi[j] : 0.0;
+            ar += vr * c - vi * s;
+            ai += vr * s + vi * c;
+        }
+        if (inverse) { ar /= n; ai /= n; }
+        yr[k] = ar;
+        yi[k] = ai;
+    }
+}
+
+/*
+ * Discrete analytic signal of a real sequence (Fig. 2 "Analytic Signal";
+ * Sec. II-B: Hilbert transform built on the FFT).  Reading: the standard
+ * one-sided-spectrum construction (Marple 1999): X = DFT(x); H[0] = 1,
+ * H[k] = 2 for 0 < k < N/2, H[N/2] = 1 for even N (for odd N, H[k] = 2 for
+ * 0 < k <= (N-1)/2), H[k] = 0 otherwise; z = IDFT(H X).
+ */
+void or_analytic(const double* x, int32_t n, double* zr, double* zi)
+{
+    double* xr = (double*)malloc(sizeof(double) * (size_t)n * 2);
+    double* xi = xr + n;
+    or_dft(x, NULL, n, 0, xr, xi);
+    for (int32_t k = 0; k < n; ++k) {
+        double h;
+        if (k == 0) h = 1.0;
+        else if (2 * k < n) h = 2.0;
+        else if (2 * k == n) h = 1.0;
+        else h = 0.0;
+        xr[k] *= h;
+        xi[k] *= h;
+    }
+    or_dft(xr, xi, n, 1, zr, zi);
+    free(xr);
+}
+
+/*
+ * Envelope = |analytic signal| along depth, per image column (Fig. 2
+ * "Analytic Signal" then "Absolute Value").  bf and env are [nz][nx];
+ * columns [col_begin, col_end) are written.
+ */
+void or_envelope(const double* bf, int32_t nz, int32_t nx, int32_t col_begin,
+                 int32_t col_end, double* env)
+{
+    double* col = (double*)malloc(sizeof(double) * (size_t)nz * 3);
+    double* zr = col + nz;
+    double* zi = zr + nz;
+    for (int32_t ix = col_begin; ix < col_end; ++ix) {
+        for (int32_t iz = 0; iz < nz; ++iz) col[iz] = bf[(size_t)iz * nx + ix];
+        or_analytic(col, nz, zr, zi);
+        for (int32_t iz = 0; iz < nz; ++iz)
+            env[(size_t)iz * nx + ix] = sqrt(zr[iz] * zr[iz] + zi[iz] * zi[iz]);
+    }
+    free(col);
+}
+
+/*
+ * Frame maximum of an envelope image, NaN values ignored (the default
+ * normalisation reference of the dynamic adjustment).  Returns 0 for an
+ * empty or all-NaN frame.
+ */
+double or_frame_max(const double* env, int64_t n)
+{
+    double m = 0.0;
+    for (int64_t i = 0; i < n; ++i)
+        if (env[i] == env[i] && env[i] > m) m = env[i];
+    return m;
+}
+
+/*
+ * Dynamic adjustment (Fig. 2 "Dynamic Adjustment"; Sec. III clips the
+ * dynamic range).  Reading: out = clamp(20 log10(max(env, 1e-30 ref) / ref),
+ * lo, hi).  A frame whose reference is not positive maps every pixel to lo;
+ * a NaN envelope value stays NaN.
+ */
+void or_logclip(const double* env, int64_t n, double ref, double lo, double hi, double* out)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double v = env[i];
+        if (v != v) { out[i] = v; continue; }
+        if (!(ref > 0.0)) { out[i] = lo; continue; }
+        double e = v > 1e-30 * ref ? v : 1e-30 * ref;
+        double db = 20.0 * log10(e / ref);
+        out[i] = db < lo ? lo : (db > hi ? hi : db);
+    }
+}

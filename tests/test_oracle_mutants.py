@@ -1,0 +1,74 @@
+"""The oracle pins catch plausible mistakes: each case plants one in a copy of oracle.c.
+
+Every mutant below is a mistake someone could make when writing the
+definitions (a dropped term, a wrong sign, swapped weights, a missing factor)
+and none of them can read out of bounds.  The copy is compiled into a
+temporary library, the pin tests run against it, and at least one of them
+must fail.
+"""
+import os
+import subprocess
+
+import pytest
+
+import oracle
+import test_oracle_pins as pins
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "oracle.c")
+
+MUTANTS = {
+    "pwi_sin_sign": ("x * sin(theta)", "-x * sin(theta)",
+                     ["test_pwi_delay_closed_forms"]),
+    "pwi_cos_for_sin": ("x * sin(theta) + z * cos(theta)", "x * cos(theta) + z * sin(theta)",
+                        ["test_pwi_delay_closed_forms"]),
+    "dropped_depth_term": ("sqrt(dx * dx + z * z)", "sqrt(dx * dx)",
+                           ["test_stai_delay_closed_forms", "test_delay_under_element_is_two_way_depth"]),
+    "stai_rx_twice": ("(or_dist(p, x, z, et) + or_dist(p, x, z, er))",
+                      "(2.0 * or_dist(p, x, z, er))", ["test_stai_delay_closed_forms"]),
+    "hann_half_missing": ("g * 0.5 * (1.0 + cos(M_PI * u))", "g * (1.0 + cos(M_PI * u))",
+                          ["test_hann_closed_forms"]),
+    "aperture_width": ("z / (2.0 * p->f_number)", "z / p->f_number", ["test_hann_closed_forms"]),
+    "lerp_weights_swapped": ("(1.0 - f) * tr[i] + f * tr[i + 1]",
+                             "f * tr[i] + (1.0 - f) * tr[i + 1]",
+                             ["test_lerp_integer_half_and_range"]),
+    "tx_weight_dropped": ("acc += wt * inner;", "acc += inner;", ["test_das_unit_rf_sums_weights"]),
+    "element_offset": ("0.5 * (double)(p->n_elements - 1)", "0.5 * (double)(p->n_elements)",
+                       ["test_element_positions_are_centred", "test_das_ramp_equals_delay"]),
+    "t_start_sign": ("- t_start * p->fs;\n}\n\n/*\n * PWI", "+ t_start * p->fs;\n}\n\n/*\n * PWI",
+                     ["test_stai_delay_closed_forms"]),
+    "one_sided_factor": ("else if (2 * k < n) h = 2.0;", "else if (2 * k < n) h = 1.0;",
+                         ["test_bin_centred_cosine_has_unit_envelope"]),
+    "inverse_scale": ("if (inverse) { ar /= n; ai /= n; }", "", ["test_dft_matches_numpy_fft"]),
+    "natural_log": ("20.0 * log10(e / ref)", "20.0 * log(e / ref)", ["test_logclip_closed_forms"]),
+}
+
+
+def _call(name, golden):
+    fn = getattr(pins, name)
+    params = {"test_bin_centred_cosine_has_unit_envelope": {"n": 64, "k0": 5},
+              "test_dft_matches_numpy_fft": {"n": 16}}.get(name, {})
+    if "golden" in fn.__code__.co_varnames[: fn.__code__.co_argcount]:
+        params["golden"] = golden
+    fn(**params)
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_planted_mistake(name, golden, tmp_path):
+    find, repl, tests = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(find) == 1, f"mutation anchor not unique: {find!r}"
+    mut = tmp_path / "oracle_mut.c"
+    mut.write_text(src.replace(find, repl))
+    so = tmp_path / "liboracle_mut.so"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared",
+                           str(mut), "-o", str(so), "-lm"])
+    for t in tests:  # the pins pass on the real oracle ...
+        _call(t, golden)
+    caught = False
+    with oracle.swap_library(str(so)):  # ... and at least one fails on the mutant
+        for t in tests:
+            try:
+                _call(t, golden)
+            except AssertionError:
+                caught = True
+    assert caught, f"no pin caught mutant {name}"
