@@ -1,0 +1,503 @@
+#!/usr/bin/env python3
+"""B-mode reconstruction throughput on GB300: frames/s of the full Fig. 2 pipeline.
+
+One step = one frame through the whole hot path: delay-and-sum (Sec. II-B),
+envelope (analytic signal + magnitude) and log-clip, for the full STAI
+workload (128 transmits x 128 receives x 2048 int16 samples, 512 x 256 grid,
+Hann apodization F = 1.5) on synthetic speckle/cyst/wire RF.  RF and outputs
+are resident in HBM for ``value``; ``e2e`` copies every frame's RF in from
+pinned host memory and the dB image back out inside the timed region.
+
+Several GPUs (torchrun) run independent replicas: the path has no exchange
+step, so there is no collective on the data path; the job throughput is the
+frames of all ranks over the slowest rank's time.
+
+``--impl reference`` times the FP64 CPU oracle on a bounded sample of the
+same workload (the deliberately slow baseline).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+import torch  # noqa: E402
+
+L2_BYTES = 129 * 1024 * 1024
+FP32_OPS_PER_DELAY_SUM = 6   # delay add, floor, fraction, 2 interpolation, 1 accumulate FMA
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--workload", default="stai_full",
+                    choices=["stai_full", "stai_small", "pwi_full_i16", "pwi_full_f16", "pwi_batch"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="CPU time budget of the oracle sample (cpu_baseline / reference arm)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graph", action="store_true")
+    return ap.parse_args()
+
+
+WORKLOAD_TEXT = {
+    "stai_full": "STAI 128 tx x 128 rx x 2048 int16, 512 (z) x 256 (x) grid 5-45 mm, Hann F=1.5, "
+                 "speckle 20k + cyst + 6 wires",
+    "stai_small": "STAI 32 tx x 32 rx x 1024 float32, 128 x 128 grid, 5 point scatterers + noise",
+    "pwi_full_i16": "PWI 64 angles (-16..16 deg) x 128 rx x 4096 int16, 1024 x 512 grid",
+    "pwi_full_f16": "PWI 64 angles (-16..16 deg) x 128 rx x 4096 float16, 1024 x 512 grid",
+    "pwi_batch": "PWI 16 frames x 16 angles x 128 rx x 2048 float32, 512 x 256 grid 5-30 mm",
+}
+
+
+def make_case(name, device):
+    from synth import configs
+    if name == "stai_full":
+        return configs.stai_full(device=device)
+    if name == "stai_small":
+        return configs.stai_small(device=device)
+    if name == "pwi_full_i16":
+        return configs.pwi_full(device=device, dtype="i16")
+    if name == "pwi_full_f16":
+        return configs.pwi_full(device=device, dtype="f16")
+    return configs.pwi_batch(device=device)
+
+
+# ----------------------------------------------------------------------------- geometry counts
+
+def delay_sum_counts(case, device):
+    """Exact (dense, aperture-active, contributing, contributing per row) delay-sum counts, FP64.
+
+    active: both weights non-zero; contributing: active and the interpolated
+    sample lies inside the record (0 <= floor(s) <= ns - 2).  Bookkeeping for
+    throughput figures only, computed with torch on ``device``.
+    """
+    f64 = torch.float64
+    e = case.n_elements
+    sc = case.fs / case.c
+    xe = (torch.arange(e, device=device, dtype=f64) - (e - 1) / 2) * case.pitch
+    xs = torch.linspace(case.x_min, case.x_max, case.nx, device=device, dtype=f64) \
+        if case.nx > 1 else torch.full((1,), case.x_min, device=device, dtype=f64)
+    zs = torch.linspace(case.z_min, case.z_max, case.nz, device=device, dtype=f64) \
+        if case.nz > 1 else torch.full((1,), case.z_min, device=device, dtype=f64)
+    n_tx = case.n_tx
+    dense = case.nz * case.nx * n_tx * e
+    active = contributing = 0
+    per_row = []
+    rows = max(1, int(2 ** 25 // (case.nx * n_tx * e)))
+    for r0 in range(0, case.nz, rows):
+        z = zs[r0:r0 + rows][:, None].expand(-1, case.nx).reshape(-1)
+        x = xs[None, :].expand(z.numel() // case.nx, -1).reshape(-1)
+        dx = xe[None, :] - x[:, None]
+        d = torch.sqrt(dx * dx + (z * z)[:, None]) * sc              # [P, E] samples
+        a = (z / (2 * case.f_number))[:, None]
+        w = (dx.abs() < a) & (a > 0) if case.apod != 2 else torch.ones_like(dx, dtype=torch.bool)
+        if case.mode == "stai":
+            tx = torch.as_tensor(case.tx_elem if case.tx_elem is not None else np.arange(n_tx),
+                                 device=device, dtype=torch.long)
+            s = d[:, tx, None] + d[:, None, :] - case.t_start * case.fs
+            act = w[:, tx, None] & w[:, None, :]
+        else:
+            th = torch.as_tensor(case.angles, device=device, dtype=f64)
+            t0 = torch.as_tensor(case.t_starts, device=device, dtype=f64) * case.fs
+            s = ((x[:, None] * torch.sin(th) + z[:, None] * torch.cos(th)) * sc - t0)[:, :, None] \
+                + d[:, None, :]
+            act = w[:, None, :].expand(-1, n_tx, -1)
+        fl = torch.floor(s)
+        ok = act & (fl >= 0) & (fl <= case.n_samples - 2)
+        active += int(act.sum())
+        row_ok = ok.reshape(-1, case.nx * n_tx * e).sum(1)
+        per_row += [int(v) for v in row_ok.cpu()]
+        contributing += int(row_ok.sum())
+    return dense, active, contributing, per_row
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples (100 ms) kept only if taken inside the marked timed region."""
+
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+        self.lines = []
+        self.window = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def region(self, t0, t1):
+        self.window = (t0, t1)
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        import datetime as dt
+        rows = []
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                ts = dt.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(parts[2]), float(parts[3]), parts[6:10]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        inside = [r for r in rows if self.window and self.window[0] <= r[0] <= self.window[1]]
+        use = inside or rows
+        reasons = sorted({n for r in use for n, f in zip(self.NAMES, r[3]) if f.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[1] for r in use), "sm_max_mhz": max(r[2] for r in use),
+                "samples": len(use), "in_timed_region": bool(inside), "reasons": reasons}
+
+
+# ----------------------------------------------------------------------------- CPU oracle sample
+
+def oracle_sample(case, seconds, counts_rows):
+    """Time the FP64 oracle on a strided subset of image rows (single thread) and scale.
+
+    Returns (frames_per_s, sample_description).  DAS time is scaled by the
+    contributing-delay-sum fraction of the sampled rows; envelope and
+    log-clip are timed on a few columns and scaled by column count.
+    """
+    import oracle
+    pr, gr = oracle.probe_grid(case)
+    rf = case.rf64[0]
+    order = list(range(0, case.nz, 7)) + [r for r in range(case.nz) if r % 7]
+    done, t_das, work = [], 0.0, 0
+    total_work = float(sum(counts_rows))
+    for r in order:
+        t0 = time.perf_counter()
+        oracle.das(case, 0, threads=1, rows=(r, r + 1))
+        t_das += time.perf_counter() - t0
+        done.append(r)
+        work += counts_rows[r]
+        if t_das > 0.85 * seconds and work > 0:
+            break
+    frac = work / total_work if total_work > 0 else len(done) / case.nz
+    das_frame = t_das / max(frac, 1e-12)
+    cols = min(case.nx, 4)
+    bf = np.random.default_rng(0).normal(size=(case.nz, cols))
+    t0 = time.perf_counter()
+    env = oracle.envelope(bf)
+    oracle.logclip(env)
+    t_post = (time.perf_counter() - t0) * case.nx / cols
+    frame = das_frame + t_post
+    desc = (f"{len(done)} of {case.nz} image rows (every 7th first; {work} of {int(total_work)} "
+            f"contributing delay-sums) + {cols} envelope/log-clip columns, single thread, "
+            f"scaled to one frame")
+    return 1.0 / frame, desc, t_das + t_post
+
+
+# ----------------------------------------------------------------------------- native arm
+
+def run_native(args, rank, world, local_rank):
+    import paper_1811_01566_gb300 as wf
+    from synth import configs  # noqa: F401
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    case = make_case(args.workload, str(dev))
+    pr = wf.Probe(case.n_elements, case.pitch, case.fs, case.c, case.f_number, case.apod)
+    gr = wf.Grid(case.nz, case.nx, case.x_min, case.x_max, case.z_min, case.z_max)
+    b = case.batch
+    rf_host = torch.from_numpy(case.rf).pin_memory()
+    rf_dev = rf_host.to(dev)
+    rf_bytes = rf_dev.numel() * rf_dev.element_size()
+    n_bufs = max(3, int(np.ceil(2 * L2_BYTES / rf_bytes)) + 1)
+    bufs = [rf_dev.clone() for _ in range(n_bufs)]
+    ws = torch.empty(wf.das_workspace_bytes(pr, gr, b, case.n_tx), dtype=torch.uint8, device=dev)
+    bf = torch.empty(b, case.nz, case.nx, device=dev)
+    env = torch.empty_like(bf)
+    db = torch.empty_like(bf)
+    fmax = torch.empty(b, device=dev)
+    if case.mode == "stai":
+        scan = dict(tx_elem=case.tx_elem, t_start=case.t_start, rf_scale=case.rf_scale)
+        das = wf.das_stai
+    else:
+        scan = dict(angles=case.angles, t_start=case.t_starts, rf_scale=case.rf_scale)
+        das = wf.das_pwi
+    stream = torch.cuda.current_stream(dev)
+
+    def step(i):
+        das(bufs[i % n_bufs], pr, gr, out=bf, workspace=ws, **scan)
+        wf.envelope(bf, out=env, frame_max=fmax)
+        wf.logclip(env, ref=fmax, out=db)
+
+    for i in range(max(3, args.warmup)):
+        step(i)
+    torch.cuda.synchronize(dev)
+    wf.workspace_check(ws)
+
+    graphs = None
+    if not args.no_graph:
+        try:
+            graphs = []
+            for i in range(n_bufs):
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g):
+                    step(i)
+                graphs.append(g)
+            for g in graphs:
+                g.replay()
+            torch.cuda.synchronize(dev)
+        except Exception as exc:  # pragma: no cover - capture problems fall back to eager
+            print(f"# graph capture unavailable ({exc}); timing eager launches", file=sys.stderr)
+            graphs = None
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    # ---- timed region: K steps, device events, max over ranks
+    with ClockSampler(local_rank) as clk:
+        t_end = time.time() + 1.0          # keep the GPU busy while nvidia-smi starts sampling
+        i = 0
+        while time.time() < t_end:
+            graphs[i % n_bufs].replay() if graphs is not None else step(i)
+            i += 1
+            if i % 64 == 0:
+                torch.cuda.synchronize(dev)
+        barrier()
+        w0 = time.time()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(args.steps):
+            if graphs is not None:
+                graphs[i % n_bufs].replay()
+            else:
+                step(i)
+        e1.record(stream)
+        barrier()
+        clk.region(w0, time.time())
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    clocks = clk.summary()
+
+    # ---- stage split (eager, events between stages on the launching stream)
+    k2 = min(args.steps, 500)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(k2)]
+    barrier()
+    for i in range(k2):
+        ev[i][0].record(stream)
+        das(bufs[i % n_bufs], pr, gr, out=bf, workspace=ws, **scan)
+        ev[i][1].record(stream)
+        wf.envelope(bf, out=env, frame_max=fmax)
+        ev[i][2].record(stream)
+        wf.logclip(env, ref=fmax, out=db)
+        ev[i][3].record(stream)
+    barrier()
+    das_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in ev)
+    env_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in ev)
+    clip_ms = statistics.mean(e[2].elapsed_time(e[3]) for e in ev)
+
+    # ---- end to end: pinned host RF in, dB image out, every step
+    db_host = torch.empty(db.shape, dtype=db.dtype, pin_memory=True)
+    rf_in = bufs[0]
+    k3 = min(args.steps, 200)
+    barrier()
+    t0 = time.perf_counter()
+    x0 = torch.cuda.Event(enable_timing=True)
+    x1 = torch.cuda.Event(enable_timing=True)
+    x0.record(stream)
+    for i in range(k3):
+        rf_in.copy_(rf_host, non_blocking=True)
+        das(rf_in, pr, gr, out=bf, workspace=ws, **scan)
+        wf.envelope(bf, out=env, frame_max=fmax)
+        wf.logclip(env, ref=fmax, out=db)
+        db_host.copy_(db, non_blocking=True)
+    x1.record(stream)
+    barrier()
+    e2e_ms = x0.elapsed_time(x1) / k3
+    wall_e2e = (time.perf_counter() - t0) / k3 * 1e3
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    wf.workspace_check(ws)
+
+    if rank != 0:
+        return None
+    dense, active, contributing, per_row = delay_sum_counts(case, dev)
+    frames = args.steps * b * world
+    fps = frames / (ms / 1e3)
+    props = torch.cuda.get_device_properties(dev)
+    peak_mhz = 2070.0
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak_mhz = float(json.load(f).get("sm_max_mhz", peak_mhz))
+    except Exception:
+        pass
+    peak_tops = props.multi_processor_count * 128 * peak_mhz * 1e6 / 1e12
+    achieved_tops = contributing * b * FP32_OPS_PER_DELAY_SUM / (das_ms / 1e3) / 1e12
+    line = {
+        "metric": "DAS frames/s (B-mode: delay-and-sum + envelope + log-clip per frame)",
+        "value": round(fps, 2),
+        "unit": "frames/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms / args.steps, 5),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {
+            "workload": f"{args.workload}: {WORKLOAD_TEXT[args.workload]}",
+            "frames_per_step": b,
+            "rf_storage": case.dtype,
+            "parallelism": "replicas" if world > 1 else "single GPU",
+            "l2": f"inputs larger than L2: {n_bufs} rotating RF copies "
+                  f"({n_bufs * rf_bytes / 2**20:.0f} MiB > 129 MB L2)",
+            "launch": "CUDA graph per step" if graphs is not None else "eager launches",
+        },
+        "delay_sums_per_frame": {"dense": dense, "aperture_active": active,
+                                 "contributing": contributing},
+        "g_delay_sums_per_s": {
+            "contributing": round(contributing * b / (das_ms / 1e3) / 1e9, 2),
+            "aperture_active": round(active * b / (das_ms / 1e3) / 1e9, 2),
+            "dense": round(dense * b / (das_ms / 1e3) / 1e9, 2)},
+        "stages_ms": {"das": round(das_ms, 5), "envelope": round(env_ms, 5),
+                      "logclip": round(clip_ms, 5)},
+        "roofline": {
+            "kernel": "wf_das_stai (tiled DAS + split reduction)" if case.mode == "stai"
+                      else "wf_das_pwi (tiled DAS + split reduction)",
+            "bound": "alu",
+            "achieved": round(achieved_tops, 3),
+            "peak": round(peak_tops, 3),
+            "unit": "Top/s (FP32 lane ops)",
+            "frac": round(achieved_tops / peak_tops, 4),
+            "traffic": None,
+            "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {peak_mhz:.0f} MHz "
+                          f"(derived from unit counts and max clock)",
+            "algorithmic": f"{FP32_OPS_PER_DELAY_SUM} FP32 ops x {contributing} contributing "
+                           f"delay-sums per frame",
+        },
+        "e2e": {"value": round(b / (e2e_ms / 1e3), 2), "unit": "frames/s",
+                "h2d_bytes_per_step": rf_bytes, "d2h_bytes_per_step": db.numel() * 4,
+                "wall_ms_per_step": round(wall_e2e, 4)},
+        "gpu_launches": 4 * args.steps,
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        cpu_case = case if case.batch == 1 else None
+        if cpu_case is not None:
+            v, desc, spent = oracle_sample(case, args.cpu_seconds, per_row)
+            line["cpu_baseline"] = {"value": round(v, 6), "unit": "frames/s", "cores": 1,
+                                    "kind": "oracle", "sample": desc,
+                                    "cpu": _cpu_model(), "seconds": round(spent, 2)}
+    return line
+
+
+def _cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith(("model name", "cpu part", "hardware")):
+                    return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return os.uname().machine
+
+
+# ----------------------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    """The FP64 CPU oracle, timed on host cores on bounded samples of the same workload."""
+    dev = "cuda" if torch.cuda.is_available() else None
+    case = make_case(args.workload, dev)
+    counts = delay_sum_counts(case, dev or "cpu")[3]
+    per_step = max(1.0, min(args.cpu_seconds, 120.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        oracle_sample(case, per_step / 4, counts)
+    vals, spent = [], 0.0
+    desc = ""
+    for _ in range(args.steps):
+        v, desc, s = oracle_sample(case, per_step, counts)
+        vals.append(v)
+        spent += s
+    fps = statistics.mean(vals)
+    line = {
+        "impl": "reference",
+        "metric": "DAS frames/s (B-mode: delay-and-sum + envelope + log-clip per frame)",
+        "value": round(fps, 6),
+        "unit": "frames/s",
+        "n_gpus": 1,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(1e3 / fps, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {WORKLOAD_TEXT[args.workload]}",
+                   "frames_per_step": 1, "parallelism": "single CPU thread"},
+        "cpu_baseline": {"value": round(fps, 6), "unit": "frames/s", "cores": 1, "kind": "oracle",
+                         "sample": desc, "cpu": _cpu_model()},
+        "e2e": {"value": round(fps, 6), "unit": "frames/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    return line
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py: the native arm needs a CUDA GPU")
+    if world > 1:
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    try:
+        line = run_native(args, rank, world, local_rank)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+    finally:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

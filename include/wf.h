@@ -1,0 +1,220 @@
+/*
+ * wf.h — C ABI of the GB300 (sm_103a) B-mode reconstruction library.
+ *
+ * The library implements the imaging pipeline of the paper's Fig. 2 as
+ * hand-written CUDA kernels:
+ *
+ *   RF channel data --wf_das_stai / wf_das_pwi--> beamformed image
+ *                   --wf_envelope--> |analytic signal| along depth
+ *                   --wf_logclip--> 20 log10(env / ref) clipped to [lo, hi] dB
+ *
+ * Sec. II-B of the paper lists the operators (DAS beamformer for synthetic
+ * transmit aperture imaging, STAI, and plane-wave imaging, PWI; envelope
+ * detection through a Hilbert transform computed with the FFT; dynamic
+ * adjustment) and Sec. II-A the metadata they consume (speed of sound,
+ * aperture, sampling frequency).  Sec. III fixes the RF layout
+ * [acquisitions, channels, samples].  The paper prints no formulas; the
+ * definitions each call implements are stated at the call.
+ *
+ * Conventions shared by every call
+ *  - Geometry: linear array on z = 0, element e at x_e = (e - (E-1)/2) pitch.
+ *    Pixel (iz, ix) at x = x_min + ix (x_max - x_min)/(nx - 1),
+ *    z = z_min + iz (z_max - z_min)/(nz - 1) (an axis of 1 pixel sits at its
+ *    minimum).  Physical quantities are SI (m, s, Hz, m/s) in double; the
+ *    library converts them to sample units once, on the host, and the
+ *    kernels work in FP32.
+ *  - Layouts: RF [batch][n_tx or n_angles][n_rx][n_samples], samples fastest.
+ *    Images [batch][nz][nx], x fastest.  All device arrays are dense.
+ *  - Ownership: the caller allocates and owns every device buffer, including
+ *    the DAS workspace.  The library never allocates, never frees and never
+ *    synchronises the stream (wf_workspace_check excepted); host arrays
+ *    passed in (transmit lists, angles, start times) are read before the call
+ *    returns and may be reused at once.
+ *  - Errors: arguments are validated on the host before any launch; a failed
+ *    check returns a status and launches nothing.  Launch failures return
+ *    WF_ERR_CUDA.  Faults inside kernels surface at the caller's next
+ *    synchronisation.  No C++ exception crosses this boundary.
+ *  - All work is enqueued on `stream` (0 = the legacy default stream).
+ */
+#ifndef WF_H_
+#define WF_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* wf_stream; /* same object as cudaStream_t */
+
+typedef enum {
+    WF_OK = 0,
+    WF_ERR_INVALID_ARG = 1, /* bad pointer, size, geometry or enum value */
+    WF_ERR_UNSUPPORTED = 2, /* valid but outside what the kernels handle (see limits) */
+    WF_ERR_CUDA = 3,        /* a CUDA launch or runtime call failed */
+    WF_ERR_WORKSPACE = 4,   /* workspace NULL or smaller than wf_das_workspace_bytes() */
+    WF_ERR_INTERNAL = 5     /* a kernel recorded an internal inconsistency */
+} wf_status;
+
+typedef enum { WF_F32 = 0, WF_F16 = 1, WF_I16 = 2 } wf_dtype;
+
+/* Apodization window over the dynamic receive aperture (see wf_das_stai). */
+typedef enum { WF_APOD_HANN = 0, WF_APOD_RECT = 1, WF_APOD_NONE = 2 } wf_apod;
+
+/* Probe and medium: Sec. II-A's metadata (aperture, sampling frequency,
+ * speed of sound) plus the receive f-number and window. */
+typedef struct {
+    int32_t n_elements;        /* E >= 1, <= WF_MAX_ELEMENTS */
+    double pitch;              /* element spacing, m, > 0 */
+    double fs;                 /* sampling frequency, Hz, > 0 */
+    double c;                  /* speed of sound, m/s, > 0 */
+    double f_number;           /* F > 0 (ignored for WF_APOD_NONE) */
+    int32_t apod;              /* wf_apod */
+    const float* elem_weight;  /* device [E] per-element weights g_e, or NULL (all 1) */
+} wf_probe;
+
+/* Pixel grid: pixel centres, bounds inclusive, x_max >= x_min, z_max >= z_min >= 0. */
+typedef struct {
+    int32_t nz, nx;            /* >= 1 each */
+    double x_min, x_max, z_min, z_max; /* m */
+} wf_grid;
+
+#define WF_MAX_ELEMENTS 1024
+#define WF_MAX_TX 256          /* transmits (STAI) or angles (PWI) per frame */
+#define WF_MAX_SAMPLES (1 << 20)
+
+/*
+ * Bytes of device workspace wf_das_stai / wf_das_pwi need for this probe,
+ * grid, batch and transmit (or angle) count.  The workspace holds the
+ * per-split partial images that the split reduction sums in a fixed order
+ * (the result is deterministic), plus a small status block.  Returns 0 if
+ * the arguments are invalid.
+ */
+size_t wf_das_workspace_bytes(const wf_probe* probe, const wf_grid* grid, int32_t batch,
+                              int32_t n_tx_or_angles);
+
+/*
+ * STAI delay-and-sum (Sec. II-B "Delay-and-Sum (DAS) beamformer ... Synthetic
+ * Transmit Aperture Imaging"; Fig. 2 "Beamforming").  For every pixel p:
+ *
+ *   b(p) = sum_t w(p, e_t) sum_r w(p, r) lerp(rf[t][r], s(p, t, r))
+ *   s(p, t, r) = (|p - x_{e_t}| + |p - x_r|) fs / c - t_start fs      (samples)
+ *
+ * with e_t = tx_elem[t] the element that fired transmit t (single-element,
+ * unfocused transmits), lerp the linear interpolation of a trace at
+ * fractional sample s (i = floor(s), f = s - i, value (1-f) x[i] + f x[i+1]
+ * when 0 <= i and i + 1 <= n_samples - 1, otherwise 0), and w the
+ * apodization: a = z / (2F), u = (x_e - x) / a, Hann 0.5 (1 + cos(pi u)) or
+ * rect 1 for |u| < 1, else 0 (no aperture for z <= 0), none = 1; times g_e.
+ * Terms with zero weight are not part of the sum.  Accumulation is FP32.
+ *
+ *  probe, grid  host structs (read during the call)
+ *  batch        frames >= 1; frame b reads rf + b * n_tx * n_rx * n_samples
+ *  n_tx         transmits per frame, 1..WF_MAX_TX
+ *  tx_elem      host [n_tx] element index of each transmit, or NULL = 0..n_tx-1
+ *  n_rx         receive channels, must equal probe->n_elements
+ *  n_samples    samples per trace, 1..WF_MAX_SAMPLES
+ *  t_start      time of sample 0 after the transmit, s
+ *  dtype        storage type of rf; WF_I16 values are multiplied by rf_scale
+ *  rf           device [batch][n_tx][n_rx][n_samples], 16-byte aligned
+ *  rf_scale     dequantisation scale for WF_I16 (ignored otherwise)
+ *  out          device float [batch][nz][nx]
+ *  ws, ws_bytes device workspace of at least wf_das_workspace_bytes() bytes
+ *  stream       CUDA stream the kernels are enqueued on
+ */
+wf_status wf_das_stai(const wf_probe* probe, const wf_grid* grid, int32_t batch,
+                      int32_t n_tx, const int32_t* tx_elem, int32_t n_rx, int32_t n_samples,
+                      double t_start, wf_dtype dtype, const void* rf, float rf_scale,
+                      float* out, void* ws, size_t ws_bytes, wf_stream stream);
+
+/*
+ * PWI delay-and-sum with coherent compounding over steering angles (Sec. II-B
+ * "Plane Wave Imaging").  For every pixel p = (x, z):
+ *
+ *   b(p) = sum_k sum_r w(p, r) lerp(rf[k][r], s(p, k, r))
+ *   s(p, k, r) = (x sin th_k + z cos th_k + |p - x_r|) fs / c - t0_k fs
+ *
+ * The plane wave of angle th_k passes (0, 0) at time 0; t0_k is the time of
+ * sample 0.  Receive apodization w as for STAI; no transmit weighting.
+ *
+ *  n_angles     angles per frame, 1..WF_MAX_TX
+ *  angles_rad   host [n_angles] steering angles, radians
+ *  t_start      host [n_angles] time of sample 0 per angle (s), or NULL = 0
+ *  other arguments as wf_das_stai; rf is [batch][n_angles][n_rx][n_samples]
+ */
+wf_status wf_das_pwi(const wf_probe* probe, const wf_grid* grid, int32_t batch,
+                     int32_t n_angles, const double* angles_rad, const double* t_start,
+                     int32_t n_rx, int32_t n_samples, wf_dtype dtype, const void* rf,
+                     float rf_scale, float* out, void* ws, size_t ws_bytes, wf_stream stream);
+
+/*
+ * FP32 delays in samples, s(p, t, r) above, exactly as the DAS kernels form
+ * them (same device code), for a list of pixels: the check that the FP32
+ * geometry path stays within its delay-error budget.
+ *
+ *  mode         0 = STAI (uses tx_elem, t_start[0]), 1 = PWI (angles_rad, t_start[k])
+ *  n_tx         transmits or angles; tx_elem/angles_rad/t_start as above (host)
+ *  n_pix, pix   device int32 [n_pix] linear pixel indices iz * nx + ix
+ *  out          device float [n_pix][n_tx][n_elements]
+ */
+wf_status wf_das_delays(const wf_probe* probe, const wf_grid* grid, int32_t mode,
+                        int32_t n_tx, const int32_t* tx_elem, const double* angles_rad,
+                        const double* t_start, int32_t n_pix, const int32_t* pix, float* out,
+                        wf_stream stream);
+
+/*
+ * Envelope detection (Fig. 2 "Analytic Signal" -> "Absolute Value"; Sec.
+ * II-B: Hilbert transform through the FFT).  For every column x of every
+ * frame, with N = nz:
+ *
+ *   Z = IDFT_N(H . DFT_N(b[:, x])),  H[0] = H[N/2] = 1, H[1..N/2-1] = 2, else 0
+ *   env[:, x] = |Z|
+ *
+ * (the discrete analytic signal).  nz must be a power of two in [2, 4096].
+ * If frame_max is not NULL it receives, per frame, the largest non-NaN
+ * envelope value (0 for an all-zero frame).
+ *
+ *  bf           device float [batch][nz][nx] (16-byte aligned)
+ *  env          device float [batch][nz][nx]; may not alias bf
+ *  frame_max    device float [batch] or NULL
+ */
+wf_status wf_envelope(const float* bf, int32_t batch, int32_t nz, int32_t nx, float* env,
+                      float* frame_max, wf_stream stream);
+
+/*
+ * Dynamic adjustment (Fig. 2 "Dynamic Adjustment"; Sec. III clips the
+ * dynamic range):
+ *
+ *   out = clamp(20 log10(max(env, 1e-30 ref) / ref), db_min, db_max)
+ *
+ * with ref = ref[b] per frame, or, when ref is NULL, the frame's largest
+ * non-NaN envelope value.  A frame whose ref is not positive maps to
+ * db_min; NaN envelope values stay NaN.  db_min <= db_max.
+ *
+ *  env          device float [batch][nz][nx]
+ *  ref          device float [batch] or NULL
+ *  out_db       device float [batch][nz][nx]; may alias env
+ */
+wf_status wf_logclip(const float* env, int32_t batch, int32_t nz, int32_t nx, const float* ref,
+                     float db_min, float db_max, float* out_db, wf_stream stream);
+
+/*
+ * Synchronises `stream` and reports whether a DAS kernel that used `ws`
+ * recorded an internal inconsistency (WF_ERR_INTERNAL) since the workspace
+ * was last handed to wf_das_stai / wf_das_pwi.  Debug aid; the only call that
+ * blocks the host.
+ */
+wf_status wf_workspace_check(const void* ws, size_t ws_bytes, wf_stream stream);
+
+/* Static, human-readable name of a status code. */
+const char* wf_status_string(wf_status status);
+
+/* Library ABI version (major * 10000 + minor * 100 + patch). */
+int32_t wf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WF_H_ */

@@ -1,0 +1,279 @@
+"""Python binding of libwf: GB300 B-mode reconstruction (DAS STAI/PWI, envelope, log-clip).
+
+Thin ctypes marshalling over the C ABI in ``include/wf.h``: every step of the
+pipeline runs in the library's CUDA kernels; PyTorch only provides device
+memory and the current stream.  There is no CPU fallback: if the compiled
+library is missing or cannot be built, importing the functions raises.
+
+Pipeline (paper Fig. 2): ``das_stai`` / ``das_pwi`` (Beamforming) ->
+``envelope`` (Analytic Signal + Absolute Value) -> ``logclip`` (Dynamic
+Adjustment); ``bmode`` chains the three.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from dataclasses import dataclass
+
+import torch
+
+from . import _build
+
+__all__ = ["Probe", "Grid", "WfError", "HANN", "RECT", "NONE", "das_stai", "das_pwi",
+           "das_workspace_bytes", "das_delays", "envelope", "logclip", "bmode",
+           "workspace_check", "library_path", "version"]
+
+HANN, RECT, NONE = 0, 1, 2
+_DTYPES = {torch.float32: 0, torch.float16: 1, torch.int16: 2}
+_STATUS = {0: "WF_OK", 1: "WF_ERR_INVALID_ARG", 2: "WF_ERR_UNSUPPORTED", 3: "WF_ERR_CUDA",
+           4: "WF_ERR_WORKSPACE", 5: "WF_ERR_INTERNAL"}
+
+
+class WfError(RuntimeError):
+    """A libwf call returned a non-OK wf_status."""
+
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {_STATUS.get(status, status)}")
+
+
+class _WfProbe(C.Structure):
+    _fields_ = [("n_elements", C.c_int32), ("pitch", C.c_double), ("fs", C.c_double),
+                ("c", C.c_double), ("f_number", C.c_double), ("apod", C.c_int32),
+                ("elem_weight", C.c_void_p)]
+
+
+class _WfGrid(C.Structure):
+    _fields_ = [("nz", C.c_int32), ("nx", C.c_int32), ("x_min", C.c_double),
+                ("x_max", C.c_double), ("z_min", C.c_double), ("z_max", C.c_double)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            if not os.path.exists(path):
+                raise ImportError(f"libwf not found at {path}")
+            lib = C.CDLL(path)
+            P, G = C.POINTER(_WfProbe), C.POINTER(_WfGrid)
+            vp, i32, f32, f64, sz = C.c_void_p, C.c_int32, C.c_float, C.c_double, C.c_size_t
+            lib.wf_das_workspace_bytes.argtypes = [P, G, i32, i32]
+            lib.wf_das_workspace_bytes.restype = sz
+            lib.wf_das_stai.argtypes = [P, G, i32, i32, vp, i32, i32, f64, i32, vp, f32, vp, vp,
+                                        sz, vp]
+            lib.wf_das_stai.restype = C.c_int
+            lib.wf_das_pwi.argtypes = [P, G, i32, i32, vp, vp, i32, i32, i32, vp, f32, vp, vp, sz,
+                                       vp]
+            lib.wf_das_pwi.restype = C.c_int
+            lib.wf_das_delays.argtypes = [P, G, i32, i32, vp, vp, vp, i32, vp, vp, vp]
+            lib.wf_das_delays.restype = C.c_int
+            lib.wf_envelope.argtypes = [vp, i32, i32, i32, vp, vp, vp]
+            lib.wf_envelope.restype = C.c_int
+            lib.wf_logclip.argtypes = [vp, i32, i32, i32, vp, f32, f32, vp, vp]
+            lib.wf_logclip.restype = C.c_int
+            lib.wf_workspace_check.argtypes = [vp, sz, vp]
+            lib.wf_workspace_check.restype = C.c_int
+            lib.wf_status_string.argtypes = [C.c_int]
+            lib.wf_status_string.restype = C.c_char_p
+            lib.wf_version.argtypes = []
+            lib.wf_version.restype = C.c_int32
+            _lib = lib
+    return _lib
+
+
+def version() -> int:
+    return _load().wf_version()
+
+
+@dataclass
+class Probe:
+    """Linear array + medium (SI units): Sec. II-A's aperture, fs and speed of sound."""
+    n_elements: int
+    pitch: float
+    fs: float
+    c: float
+    f_number: float = 1.5
+    apod: int = HANN
+    elem_weight: torch.Tensor | None = None   # CUDA float32 [n_elements] or None
+
+    def _c(self):
+        w = self.elem_weight
+        if w is not None:
+            if not (w.is_cuda and w.dtype == torch.float32 and w.is_contiguous()
+                    and w.numel() == self.n_elements):
+                raise ValueError("elem_weight must be a contiguous CUDA float32 [n_elements] tensor")
+        return _WfProbe(int(self.n_elements), float(self.pitch), float(self.fs), float(self.c),
+                        float(self.f_number), int(self.apod), w.data_ptr() if w is not None else None)
+
+
+@dataclass
+class Grid:
+    """Pixel grid: nz x nx pixel centres over [x_min, x_max] x [z_min, z_max] (m)."""
+    nz: int
+    nx: int
+    x_min: float
+    x_max: float
+    z_min: float
+    z_max: float
+
+    def _c(self):
+        return _WfGrid(int(self.nz), int(self.nx), float(self.x_min), float(self.x_max),
+                       float(self.z_min), float(self.z_max))
+
+
+def _stream(stream):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise WfError(status, where)
+
+
+def _as_frames(rf: torch.Tensor) -> torch.Tensor:
+    if rf.dim() == 3:
+        rf = rf.unsqueeze(0)
+    if rf.dim() != 4:
+        raise ValueError("rf must be [batch, n_tx, n_rx, n_samples] or [n_tx, n_rx, n_samples]")
+    if not rf.is_cuda or rf.dtype not in _DTYPES or not rf.is_contiguous():
+        raise ValueError("rf must be a contiguous CUDA float32/float16/int16 tensor")
+    return rf
+
+
+def das_workspace_bytes(probe: Probe, grid: Grid, batch: int, n_tx: int) -> int:
+    n = _load().wf_das_workspace_bytes(C.byref(probe._c()), C.byref(grid._c()), int(batch),
+                                       int(n_tx))
+    if n == 0:
+        raise WfError(1, "wf_das_workspace_bytes")
+    return int(n)
+
+
+def _prep(rf, probe, grid, out, workspace):
+    rf = _as_frames(rf)
+    b, n_tx, n_rx, ns = rf.shape
+    if out is None:
+        out = torch.empty(b, grid.nz, grid.nx, device=rf.device, dtype=torch.float32)
+    need = das_workspace_bytes(probe, grid, b, n_tx)
+    if workspace is None:
+        workspace = torch.empty(need, device=rf.device, dtype=torch.uint8)
+    return rf, out, workspace
+
+
+def das_stai(rf: torch.Tensor, probe: Probe, grid: Grid, *, tx_elem=None, t_start: float = 0.0,
+             rf_scale: float = 1.0, out: torch.Tensor | None = None,
+             workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """STAI delay-and-sum -> beamformed image [batch, nz, nx] (float32); see wf_das_stai."""
+    rf, out, ws = _prep(rf, probe, grid, out, workspace)
+    b, n_tx, n_rx, ns = rf.shape
+    tx = None
+    if tx_elem is not None:
+        tx = (C.c_int32 * n_tx)(*[int(v) for v in tx_elem])
+    st = _load().wf_das_stai(C.byref(probe._c()), C.byref(grid._c()), b, n_tx, tx, n_rx, ns,
+                             float(t_start), _DTYPES[rf.dtype], rf.data_ptr(), float(rf_scale),
+                             out.data_ptr(), ws.data_ptr(), ws.numel() * ws.element_size(),
+                             _stream(stream))
+    _check(st, "wf_das_stai")
+    return out
+
+
+def das_pwi(rf: torch.Tensor, probe: Probe, grid: Grid, *, angles, t_start=None,
+            rf_scale: float = 1.0, out: torch.Tensor | None = None,
+            workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """PWI delay-and-sum with coherent compounding -> [batch, nz, nx] (float32); see wf_das_pwi."""
+    rf, out, ws = _prep(rf, probe, grid, out, workspace)
+    b, n_ang, n_rx, ns = rf.shape
+    ang = (C.c_double * n_ang)(*[float(v) for v in angles])
+    ts = None if t_start is None else (C.c_double * n_ang)(*[float(v) for v in t_start])
+    st = _load().wf_das_pwi(C.byref(probe._c()), C.byref(grid._c()), b, n_ang, ang, ts, n_rx, ns,
+                            _DTYPES[rf.dtype], rf.data_ptr(), float(rf_scale), out.data_ptr(),
+                            ws.data_ptr(), ws.numel() * ws.element_size(), _stream(stream))
+    _check(st, "wf_das_pwi")
+    return out
+
+
+def das_delays(probe: Probe, grid: Grid, mode: str, pix: torch.Tensor, *, n_tx: int,
+               tx_elem=None, angles=None, t_start=None, stream=None) -> torch.Tensor:
+    """FP32 delays (samples) the DAS kernels use: [n_pix, n_tx, n_elements]."""
+    if not (pix.is_cuda and pix.dtype == torch.int32 and pix.is_contiguous()):
+        raise ValueError("pix must be a contiguous CUDA int32 tensor")
+    out = torch.empty(pix.numel(), n_tx, probe.n_elements, device=pix.device, dtype=torch.float32)
+    tx = None if tx_elem is None else (C.c_int32 * n_tx)(*[int(v) for v in tx_elem])
+    ang = None if angles is None else (C.c_double * n_tx)(*[float(v) for v in angles])
+    if t_start is None:
+        ts = None
+    else:
+        vals = [float(t_start)] if mode == "stai" and not hasattr(t_start, "__len__") else \
+            [float(v) for v in t_start]
+        ts = (C.c_double * len(vals))(*vals)
+    st = _load().wf_das_delays(C.byref(probe._c()), C.byref(grid._c()), 0 if mode == "stai" else 1,
+                               int(n_tx), tx, ang, ts, pix.numel(), pix.data_ptr(), out.data_ptr(),
+                               _stream(stream))
+    _check(st, "wf_das_delays")
+    return out
+
+
+def envelope(bf: torch.Tensor, *, out: torch.Tensor | None = None, with_max: bool = True,
+             frame_max: torch.Tensor | None = None, stream=None):
+    """|analytic signal| along depth of [batch, nz, nx] -> (env, frame_max or None)."""
+    if bf.dim() == 2:
+        bf = bf.unsqueeze(0)
+    if not (bf.is_cuda and bf.dtype == torch.float32 and bf.is_contiguous()):
+        raise ValueError("bf must be a contiguous CUDA float32 tensor")
+    b, nz, nx = bf.shape
+    if out is None:
+        out = torch.empty_like(bf)
+    if with_max and frame_max is None:
+        frame_max = torch.empty(b, device=bf.device, dtype=torch.float32)
+    fm = frame_max.data_ptr() if (with_max and frame_max is not None) else None
+    st = _load().wf_envelope(bf.data_ptr(), b, nz, nx, out.data_ptr(), fm, _stream(stream))
+    _check(st, "wf_envelope")
+    return out, (frame_max if with_max else None)
+
+
+def logclip(env: torch.Tensor, *, ref: torch.Tensor | None = None, db_min: float = -60.0,
+            db_max: float = 0.0, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """clamp(20 log10(env / ref), db_min, db_max) of [batch, nz, nx]; ref None = frame max."""
+    if env.dim() == 2:
+        env = env.unsqueeze(0)
+    if not (env.is_cuda and env.dtype == torch.float32 and env.is_contiguous()):
+        raise ValueError("env must be a contiguous CUDA float32 tensor")
+    b, nz, nx = env.shape
+    if out is None:
+        out = torch.empty_like(env)
+    if ref is not None and not (ref.is_cuda and ref.dtype == torch.float32 and ref.numel() == b):
+        raise ValueError("ref must be a CUDA float32 [batch] tensor")
+    st = _load().wf_logclip(env.data_ptr(), b, nz, nx, None if ref is None else ref.data_ptr(),
+                            float(db_min), float(db_max), out.data_ptr(), _stream(stream))
+    _check(st, "wf_logclip")
+    return out
+
+
+def bmode(rf: torch.Tensor, probe: Probe, grid: Grid, *, mode: str, db_min: float = -60.0,
+          db_max: float = 0.0, workspace: torch.Tensor | None = None, stream=None, **scan):
+    """Whole Fig. 2 pipeline: returns (beamformed, envelope, dB image), each [batch, nz, nx]."""
+    if mode == "stai":
+        bf = das_stai(rf, probe, grid, workspace=workspace, stream=stream, **scan)
+    elif mode == "pwi":
+        bf = das_pwi(rf, probe, grid, workspace=workspace, stream=stream, **scan)
+    else:
+        raise ValueError("mode must be 'stai' or 'pwi'")
+    env, fmax = envelope(bf, stream=stream)
+    return bf, env, logclip(env, ref=fmax, db_min=db_min, db_max=db_max, stream=stream)
+
+
+def workspace_check(workspace: torch.Tensor, stream=None) -> None:
+    """Synchronise and raise WfError(WF_ERR_INTERNAL) if a DAS kernel flagged the workspace."""
+    st = _load().wf_workspace_check(workspace.data_ptr(), workspace.numel() * workspace.element_size(),
+                                    _stream(stream))
+    _check(st, "wf_workspace_check")

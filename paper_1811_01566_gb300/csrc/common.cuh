@@ -1,0 +1,89 @@
+// Internal helpers shared by the CUDA translation units of libwf (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "wf.h"
+
+namespace wf {
+
+// ---------------------------------------------------------------------------
+// Host-side status plumbing.
+// ---------------------------------------------------------------------------
+inline wf_status cuda_status(cudaError_t e) { return e == cudaSuccess ? WF_OK : WF_ERR_CUDA; }
+
+// Raise a kernel's dynamic shared-memory limit to `bytes` once per device.
+// Done outside stream capture on the first call for a device (the attribute
+// is not a stream operation), so later calls can be captured in CUDA graphs.
+template <typename K>
+inline wf_status ensure_smem_limit(K kernel, size_t bytes, unsigned long long& done_mask) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return WF_ERR_CUDA;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (__atomic_load_n(&done_mask, __ATOMIC_ACQUIRE) & bit) return WF_OK;
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+        cudaSuccess)
+        return WF_ERR_CUDA;
+    __atomic_fetch_or(&done_mask, bit, __ATOMIC_ACQ_REL);
+    return WF_OK;
+}
+
+inline wf_status last_launch_status() {
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? WF_OK : WF_ERR_CUDA;
+}
+
+// Status block at the head of every DAS workspace (device side).
+struct WsHeader {
+    unsigned int flags;   // bit 0: staging window overflow, bit 1: gather index out of window
+    unsigned int first_bad[3];
+    unsigned int pad[60];
+};
+static_assert(sizeof(WsHeader) == 256, "workspace header is 256 bytes");
+constexpr size_t kWsHeaderBytes = 256;
+
+// ---------------------------------------------------------------------------
+// Geometry in sample units.  The host converts every physical length to
+// samples (multiplying by fs / c) in double and rounds once to float, so a
+// distance d in samples is directly a delay.
+// ---------------------------------------------------------------------------
+struct Geom {
+    float gx0, gdx;     // pixel x: gx0 + ix * gdx (samples)
+    float gz0, gdz;     // pixel z: gz0 + iz * gdz (samples)
+    float xe0, pitch;   // element x: xe0 + e * pitch (samples)
+    float two_f;        // 2 F: aperture scale, u = (x_e - x) * 2F / z
+    int apod;           // wf_apod
+    int n_elements;
+    int nz, nx;
+    const float* elem_weight;  // device [E] or nullptr
+};
+
+__device__ __forceinline__ float pixel_x(const Geom& g, int ix) { return fmaf((float)ix, g.gdx, g.gx0); }
+__device__ __forceinline__ float pixel_z(const Geom& g, int iz) { return fmaf((float)iz, g.gdz, g.gz0); }
+__device__ __forceinline__ float elem_x(const Geom& g, int e) { return fmaf((float)e, g.pitch, g.xe0); }
+
+// One-way element-to-pixel distance (samples); z2 = z * z of the pixel.
+__device__ __forceinline__ float elem_dist(float xe, float px, float z2) {
+    float dx = xe - px;
+    return __fsqrt_rn(fmaf(dx, dx, z2));
+}
+
+// Receive/transmit apodization of the element at xe for a pixel with
+// inverse half-aperture kap = 2F / z (kap <= 0 or non-finite: no aperture).
+// Hann: 0.5 (1 + cos(pi u)) for |u| < 1; rect: 1 for |u| < 1; none: 1.
+__device__ __forceinline__ float apod_weight(int apod, float xe, float px, float kap) {
+    if (apod == WF_APOD_NONE) return 1.0f;
+    float u = (xe - px) * kap;
+    if (!(kap > 0.0f) || !(fabsf(u) < 1.0f)) return 0.0f;
+    if (apod == WF_APOD_RECT) return 1.0f;
+    return fmaf(0.5f, cospif(u), 0.5f);
+}
+
+// Inverse half-aperture 2F / z of a pixel (0 when z <= 0: no aperture).
+__device__ __forceinline__ float aperture_kappa(const Geom& g, float pz) {
+    return pz > 0.0f ? g.two_f / pz : 0.0f;
+}
+
+}  // namespace wf

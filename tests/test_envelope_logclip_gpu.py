@@ -1,0 +1,84 @@
+"""GPU parity of wf_envelope and wf_logclip against the FP64 oracle (Fig. 2 post-processing)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1811_01566_gb300 as wf
+from helpers import THREADS
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("nz,nx,batch", [(2, 3, 1), (4, 1, 1), (8, 7, 2), (64, 33, 1),
+                                         (128, 128, 1), (256, 9, 3), (512, 256, 1),
+                                         (1024, 65, 1), (2048, 4, 1), (4096, 3, 2)])
+def test_envelope_matches_oracle(nz, nx, batch):
+    rng = np.random.default_rng(nz + nx)
+    bf = rng.normal(size=(batch, nz, nx)).astype(np.float32)
+    env, fmax = wf.envelope(torch.from_numpy(bf).cuda())
+    env = env.cpu().numpy()
+    for b in range(batch):
+        want = oracle.envelope(bf[b].astype(np.float64), threads=THREADS)
+        err = np.abs(env[b] - want).max() / np.abs(want).max()
+        assert err < 2e-6 * max(1.0, math.log2(nz)), err
+        assert fmax[b].item() == pytest.approx(oracle.frame_max(want), rel=1e-5)
+        assert fmax[b].item() == env[b].max()
+
+
+@pytest.mark.parametrize("n,k0", [(64, 3), (512, 100), (4096, 1000)])
+def test_envelope_of_bin_centred_cosine_is_one(n, k0):
+    t = np.arange(n)
+    cols = np.stack([np.cos(2 * np.pi * k0 * t / n), np.sin(2 * np.pi * (k0 + 1) * t / n),
+                     np.full(n, 0.75)], axis=1).astype(np.float32)
+    env, _ = wf.envelope(torch.from_numpy(cols).cuda())
+    env = env[0].cpu().numpy()
+    np.testing.assert_allclose(env[:, :2], 1.0, atol=2e-5)
+    np.testing.assert_allclose(env[:, 2], 0.75, atol=1e-6)
+
+
+def test_envelope_without_max_and_nan_column():
+    bf = torch.randn(1, 64, 8, device="cuda")
+    bf[0, 5, 3] = float("nan")
+    env, fmax = wf.envelope(bf, with_max=False)
+    assert fmax is None
+    e = env[0].cpu().numpy()
+    assert np.isnan(e[:, 3]).all() and not np.isnan(np.delete(e, 3, axis=1)).any()
+    _, fmax = wf.envelope(bf)
+    assert math.isfinite(fmax.item()) and fmax.item() > 0
+
+
+@pytest.mark.parametrize("nz,nx,batch", [(1, 1, 1), (7, 5, 2), (512, 256, 1), (1024, 512, 2),
+                                         (100, 1000, 3)])
+@pytest.mark.parametrize("given_ref", [False, True])
+def test_logclip_matches_oracle(nz, nx, batch, given_ref):
+    rng = np.random.default_rng(nz * nx)
+    env = (rng.rayleigh(size=(batch, nz, nx)) * 10 ** rng.uniform(-4, 0, size=(batch, nz, nx))
+           ).astype(np.float32)
+    env[0, 0, 0] = 0.0
+    ref = (np.abs(env).reshape(batch, -1).max(1) * 0.5).astype(np.float32) if given_ref else None
+    out = wf.logclip(torch.from_numpy(env).cuda(),
+                     ref=None if ref is None else torch.from_numpy(ref).cuda(),
+                     db_min=-60.0, db_max=0.0).cpu().numpy()
+    for b in range(batch):
+        want = oracle.logclip(env[b].astype(np.float64), None if ref is None else float(ref[b]),
+                              -60.0, 0.0)
+        assert np.abs(out[b] - want).max() <= 1e-3
+
+
+def test_logclip_edge_values():
+    env = torch.tensor([[[1.0, 0.01, 0.0, 2.0, float("nan")]]], device="cuda")
+    out = wf.logclip(env, ref=torch.tensor([1.0], device="cuda")).cpu().numpy()[0, 0]
+    np.testing.assert_allclose(out[:4], [0.0, -40.0, -60.0, 0.0], atol=1e-4)
+    assert math.isnan(out[4])
+    out = wf.logclip(env, ref=torch.tensor([0.0], device="cuda")).cpu().numpy()[0, 0]
+    np.testing.assert_allclose(out[:4], -60.0)
+    out = wf.logclip(env, ref=torch.tensor([1.0], device="cuda"), db_min=0.0, db_max=30.0)
+    assert out[0, 0, 3].item() == pytest.approx(20 * math.log10(2.0), abs=1e-4)
+    zero = wf.logclip(torch.zeros(2, 33, 17, device="cuda"))
+    assert (zero == -60.0).all()
+    inplace = env.clone()
+    wf.logclip(inplace, out=inplace)
+    assert inplace[0, 0, 0].item() == 0.0     # frame max 2.0: 20 log10(1/2)
