@@ -149,18 +149,21 @@ wf_status wf_das_pwi(const wf_probe* probe, const wf_grid* grid, int32_t batch,
                      float rf_scale, float* out, void* ws, size_t ws_bytes, wf_stream stream);
 
 /*
- * FP32 delays in samples, s(p, t, r) above, exactly as the DAS kernels form
- * them (same device code), for a list of pixels: the check that the FP32
- * geometry path stays within its delay-error budget.
+ * Delays in samples, s(p, t, r) above, exactly as the tiled DAS kernel forms
+ * them (same device code): the integer start of the staging window plus the
+ * FP32 window-relative delay.  This is the check that the FP32 geometry path
+ * stays within its delay-error budget.  Triples the DAS kernels never
+ * evaluate (receive element outside the pixel tile's aperture range, STAI
+ * transmit element outside it) are NaN.
  *
  *  mode         0 = STAI (uses tx_elem, t_start[0]), 1 = PWI (angles_rad, t_start[k])
  *  n_tx         transmits or angles; tx_elem/angles_rad/t_start as above (host)
  *  n_pix, pix   device int32 [n_pix] linear pixel indices iz * nx + ix
- *  out          device float [n_pix][n_tx][n_elements]
+ *  out          device double [n_pix][n_tx][n_elements]
  */
 wf_status wf_das_delays(const wf_probe* probe, const wf_grid* grid, int32_t mode,
                         int32_t n_tx, const int32_t* tx_elem, const double* angles_rad,
-                        const double* t_start, int32_t n_pix, const int32_t* pix, float* out,
+                        const double* t_start, int32_t n_pix, const int32_t* pix, double* out,
                         wf_stream stream);
 
 /*
@@ -173,7 +176,9 @@ wf_status wf_das_delays(const wf_probe* probe, const wf_grid* grid, int32_t mode
  *
  * (the discrete analytic signal).  nz must be a power of two in [2, 4096].
  * If frame_max is not NULL it receives, per frame, the largest non-NaN
- * envelope value (0 for an all-zero frame).
+ * envelope value (0 for an all-zero frame).  Columns are transformed in
+ * pairs (x = 2m, 2m+1) through one complex FFT, so a NaN or Inf anywhere in a
+ * column also reaches the envelope of its pair partner.
  *
  *  bf           device float [batch][nz][nx] (16-byte aligned)
  *  env          device float [batch][nz][nx]; may not alias bf

@@ -204,10 +204,10 @@ def das_pwi(rf: torch.Tensor, probe: Probe, grid: Grid, *, angles, t_start=None,
 
 def das_delays(probe: Probe, grid: Grid, mode: str, pix: torch.Tensor, *, n_tx: int,
                tx_elem=None, angles=None, t_start=None, stream=None) -> torch.Tensor:
-    """FP32 delays (samples) the DAS kernels use: [n_pix, n_tx, n_elements]."""
+    """Delays (samples) the DAS kernels use: float64 [n_pix, n_tx, n_elements], NaN where unused."""
     if not (pix.is_cuda and pix.dtype == torch.int32 and pix.is_contiguous()):
         raise ValueError("pix must be a contiguous CUDA int32 tensor")
-    out = torch.empty(pix.numel(), n_tx, probe.n_elements, device=pix.device, dtype=torch.float32)
+    out = torch.empty(pix.numel(), n_tx, probe.n_elements, device=pix.device, dtype=torch.float64)
     tx = None if tx_elem is None else (C.c_int32 * n_tx)(*[int(v) for v in tx_elem])
     ang = None if angles is None else (C.c_double * n_tx)(*[float(v) for v in angles])
     if t_start is None:

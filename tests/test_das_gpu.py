@@ -102,7 +102,7 @@ def test_deterministic_and_bounds_check_mode(monkeypatch):
 
 
 def test_nan_in_active_sample_propagates():
-    case = configs.random_case("stai", 5, n_elements=8, n_tx=8, n_samples=600, nz=10, nx=10,
+    case = configs.random_case("stai", 5, n_elements=8, n_tx=8, n_samples=1500, nz=10, nx=10,
                                apod=configs.NONE)
     pr, gr = oracle.probe_grid(case)
     x, z = oracle.pixel_xz(gr, 5, 5)
@@ -132,30 +132,44 @@ def test_workspace_too_small_raises():
 
 @pytest.mark.parametrize("mode", ["stai", "pwi"])
 def test_fp32_delay_error_below_budget(mode):
-    """FP32 delays of the kernels vs FP64 delays: <= 1e-3 samples on the full-size geometries."""
+    """Kernel delays vs FP64 delays: <= 1e-3 samples on the full-size geometries.
+
+    Every (pixel, transmit, element) triple with non-zero weights must be
+    evaluated by the kernel (finite probe value); the error is taken over all
+    evaluated triples.
+    """
+    e = 128
     if mode == "stai":
-        e, nz, nx, n_tx, ang = 128, 512, 256, 128, None
-        zr = (5e-3, 45e-3)
+        nz, nx, n_tx, ang = 512, 256, 128, None
     else:
-        e, nz, nx, n_tx = 128, 1024, 512, 64
+        nz, nx, n_tx = 1024, 512, 64
         ang = np.deg2rad(np.linspace(-16, 16, n_tx))
-        zr = (5e-3, 45e-3)
+    zr = (5e-3, 45e-3)
     span = (e - 1) / 2 * 0.3e-3
     pr = wf.Probe(e, 0.3e-3, 50e6, 1540.0)
     gr = wf.Grid(nz, nx, -span, span, zr[0], zr[1])
     opr = oracle.Probe(e, 0.3e-3, 50e6, 1540.0)
     ogr = oracle.Grid(nz, nx, -span, span, zr[0], zr[1])
     rng = np.random.default_rng(0)
-    pix = np.concatenate([[0, nz * nx - 1, nx - 1, (nz - 1) * nx], rng.integers(0, nz * nx, 60)])
+    pix = np.concatenate([[0, nz * nx - 1, nx - 1, (nz - 1) * nx], rng.integers(0, nz * nx, 40)])
     d = wf.das_delays(pr, gr, mode, torch.tensor(pix, dtype=torch.int32, device="cuda"),
-                      n_tx=n_tx, angles=ang).cpu().numpy().astype(np.float64)
-    worst = 0.0
+                      n_tx=n_tx, angles=ang).cpu().numpy()
+    worst, n_eval = 0.0, 0
     for q, lin in enumerate(pix):
         x, z = oracle.pixel_xz(ogr, int(lin // nx), int(lin % nx))
+        w = np.array([oracle.apod(opr, x, z, r) for r in range(e)])
         for t in range(n_tx):
             if mode == "stai":
                 ref = np.array([oracle.delay_stai(opr, x, z, t, r) for r in range(e)])
+                need = (w[t] != 0) & (w != 0)
             else:
                 ref = np.array([oracle.delay_pwi(opr, x, z, ang[t], r) for r in range(e)])
-            worst = max(worst, float(np.abs(d[q, t] - ref).max()))
+                need = w != 0
+            got = d[q, t]
+            assert np.isfinite(got[need]).all()
+            ok = np.isfinite(got)
+            n_eval += int(ok.sum())
+            if ok.any():
+                worst = max(worst, float(np.abs(got[ok] - ref[ok]).max()))
+    assert n_eval > 0
     assert worst <= 1e-3, worst
