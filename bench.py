@@ -47,6 +47,8 @@ def parse():
                     help="CPU time budget of the oracle sample (cpu_baseline / reference arm)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--profile-only", action="store_true",
+                    help="only W + K eager pipeline steps (a short, clean command for ncu)")
     return ap.parse_args()
 
 
@@ -259,6 +261,11 @@ def run_native(args, rank, world, local_rank):
         step(i)
     torch.cuda.synchronize(dev)
     wf.workspace_check(ws)
+    if args.profile_only:
+        for i in range(args.steps):
+            step(i)
+        torch.cuda.synchronize(dev)
+        return None
 
     graphs = None
     if not args.no_graph:
@@ -492,7 +499,7 @@ def main():
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     try:
         line = run_native(args, rank, world, local_rank)
-        if rank == 0:
+        if rank == 0 and line is not None:
             print(json.dumps(line), flush=True)
     finally:
         if world > 1:

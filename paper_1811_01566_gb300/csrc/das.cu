@@ -34,14 +34,11 @@
 
 namespace wf {
 
-constexpr int kTZ = 16;                    // tile rows (z)
-constexpr int kTX = 32;                    // tile columns (x) = lanes
-constexpr int kThreads = 256;              // 8 warps
-constexpr int kP = kTZ / (kThreads / 32);  // pixels (rows) per thread
-constexpr int kTilePix = kTZ * kTX;
+constexpr int kTX = 32;                    // tile columns (x): 8 warps x 4 columns
+constexpr int kThreads = 256;              // 8 warps; lane = (row 0..7) * 4 + (column 0..3)
 constexpr int kC = 8;                      // receive elements per chunk
 constexpr int kTS = 8;                     // transmits per slice
-constexpr int kMaxWindow = 2048;           // staged positions per trace
+constexpr int kMaxWindow = 512;            // staged positions per trace (2 segments/thread)
 constexpr float kMagic = 12582912.0f;      // 1.5 * 2^23
 constexpr int kMagicBits = 0x4B400000;
 
@@ -63,10 +60,11 @@ struct DasArgs {
     int n_tx, ns;
     int tiles_x, n_slices, n_items;  // items per frame = tiles * slices
     int W;                           // staged positions per trace (shared stride)
+    int P;                           // tile rows / 8 (pixels per thread)
     const void* rf;
     float rf_scale;
     long long frame_elems;           // n_tx * E * ns
-    float* part;                     // [batch][n_items][kTilePix]
+    float* part;                     // [batch][n_items][256 * P] slice partials
     float* out;                      // direct kernel only
     WsHeader* hdr;
     TxInfo tx[WF_MAX_TX];
@@ -161,32 +159,34 @@ __device__ __forceinline__ int2 tile_elements(const Geom& g, float xlo, float xh
     return make_int2(max(lo, 0), min(hi, g.n_elements - 1));
 }
 
-// Range [min, max] of the transmit term over the tile rectangle (FP32, for windows).
+// Exact range over the rectangle [xlo, xhi] x [zlo, zhi] of the delay of one
+// (transmit, receive element) pair, FP32.  Both delay forms are convex in x
+// and increase with z >= 0, so the maximum sits on a bottom corner and the
+// minimum on the top edge at the clamped stationary point: the midpoint of
+// the two elements for STAI, x_r - z tan(th) for PWI.
 template <int MODE>
-__device__ __forceinline__ float2 tx_bounds(const Geom& g, const TxInfo& ti, float xlo, float xhi,
-                                            float zlo, float zhi) {
+__device__ __forceinline__ float2 pair_bounds(const Geom& g, const TxInfo& ti, int r, float xlo,
+                                              float xhi, float zlo, float zhi) {
+    const float xr = elem_x(g, r);
     const float c = (float)(-ti.t0_d);
     if (MODE == 0) {
-        const float xe = elem_x(g, ti.e);
-        const float dxm = fmaxf(0.0f, fmaxf(xlo - xe, xe - xhi));
-        const float dfar = fmaxf(fabsf(xe - xlo), fabsf(xe - xhi));
-        return make_float2(__fsqrt_rn(fmaf(dxm, dxm, zlo * zlo)) + c,
-                           __fsqrt_rn(fmaf(dfar, dfar, zhi * zhi)) + c);
+        const float xt = elem_x(g, ti.e);
+        const float xm = fminf(fmaxf(0.5f * (xt + xr), xlo), xhi);
+        const float a0 = xm - xt, b0 = xm - xr;
+        const float mn = sqrtf(fmaf(a0, a0, zlo * zlo)) + sqrtf(fmaf(b0, b0, zlo * zlo));
+        const float a1 = xlo - xt, b1 = xlo - xr, a2 = xhi - xt, b2 = xhi - xr;
+        const float z2 = zhi * zhi;
+        const float mx = fmaxf(sqrtf(fmaf(a1, a1, z2)) + sqrtf(fmaf(b1, b1, z2)),
+                               sqrtf(fmaf(a2, a2, z2)) + sqrtf(fmaf(b2, b2, z2)));
+        return make_float2(mn + c, mx + c);
     }
-    const float v0 = fmaf(xlo, ti.sin_f, fmaf(zlo, ti.cos_f, c));
-    const float v1 = fmaf(xhi, ti.sin_f, fmaf(zlo, ti.cos_f, c));
-    const float v2 = fmaf(xlo, ti.sin_f, fmaf(zhi, ti.cos_f, c));
-    const float v3 = fmaf(xhi, ti.sin_f, fmaf(zhi, ti.cos_f, c));
-    return make_float2(fminf(fminf(v0, v1), fminf(v2, v3)), fmaxf(fmaxf(v0, v1), fmaxf(v2, v3)));
-}
-
-// Range of the receive distance over the tile rectangle and elements [r0, r1].
-__device__ __forceinline__ float2 rx_bounds(const Geom& g, int r0, int r1, float xlo, float xhi,
-                                            float zlo, float zhi) {
-    const float xa = elem_x(g, r0), xb = elem_x(g, r1);
-    const float dxm = fmaxf(0.0f, fmaxf(xlo - xb, xa - xhi));
-    const float dfar = fmaxf(xb - xlo, xhi - xa);
-    return make_float2(__fsqrt_rn(fmaf(dxm, dxm, zlo * zlo)), __fsqrt_rn(fmaf(dfar, dfar, zhi * zhi)));
+    const float xm = fminf(fmaxf(xr - zlo * (ti.sin_f / ti.cos_f), xlo), xhi);
+    const float b0 = xm - xr;
+    const float mn = fmaf(xm, ti.sin_f, zlo * ti.cos_f) + sqrtf(fmaf(b0, b0, zlo * zlo));
+    const float b1 = xlo - xr, b2 = xhi - xr, z2 = zhi * zhi;
+    const float mx = fmaxf(fmaf(xlo, ti.sin_f, zhi * ti.cos_f) + sqrtf(fmaf(b1, b1, z2)),
+                           fmaf(xhi, ti.sin_f, zhi * ti.cos_f) + sqrtf(fmaf(b2, b2, z2)));
+    return make_float2(mn + c, mx + c);
 }
 
 // Transmit reference term (FP64).
@@ -204,14 +204,16 @@ __device__ __forceinline__ void flag(WsHeader* h, unsigned bit, unsigned a, unsi
     }
 }
 
-// Tile geometry shared by the DAS kernel and the delay probe.
+// Tile geometry shared by the DAS kernel and the delay probe.  A tile is
+// kTX columns by 8 P rows; its origin pixel is the FP64 reference point.
 struct TileGeo {
     int ix0, iz0;
-    double cx, cz;            // reference point = tile origin pixel (FP64 samples)
+    double cx, cz;            // reference point (FP64 samples)
     float xlo, xhi, zlo, zhi; // tile rectangle (FP32 samples)
     int2 er;                  // element range
 };
 
+template <int P>
 __device__ __forceinline__ TileGeo tile_geo(const DasArgs& a, int ix0, int iz0) {
     const Geom& g = a.g;
     TileGeo t;
@@ -222,59 +224,227 @@ __device__ __forceinline__ TileGeo tile_geo(const DasArgs& a, int ix0, int iz0) 
     t.xlo = pixel_x(g, ix0);
     t.xhi = pixel_x(g, ix0 + kTX - 1);
     t.zlo = pixel_z(g, iz0);
-    t.zhi = pixel_z(g, iz0 + kTZ - 1);
+    t.zhi = pixel_z(g, iz0 + 8 * P - 1);
     t.er = tile_elements(g, t.xlo, t.xhi, t.zhi);
     return t;
 }
 
-// Staging window of (transmit term bounds tb, chunk starting at r0): lo, len
-// and the FP32 window-relative base B = tx_ref + R_{r0} - lo.
+// Staging window of one (transmit, receive chunk) stage: the first staged
+// sample lo (multiple of 8), the staged length (multiple of 8), and the FP32
+// window-relative base B = tx_ref + R_{r0} - lo.
 struct StageInfo {
-    int lo, len, skip, pad;
+    int lo, len, skip, over;   // over: the window was longer than the shared stride (clamped)
     float B;
     float pad2[3];
 };
 
-__device__ __forceinline__ StageInfo stage_info(const DasArgs& a, const TileGeo& tg, float2 tb,
-                                                double txref, int r0, int r_last, double R_r0) {
-    const float2 rb = rx_bounds(a.g, r0, r_last, tg.xlo, tg.xhi, tg.zlo, tg.zhi);
+__device__ __forceinline__ StageInfo make_stage(const DasArgs& a, float mn, float mx, double txref,
+                                                double R_r0) {
     StageInfo si;
-    si.lo = (int)floorf(tb.x + rb.x) - 2;
-    si.len = (int)ceilf(tb.y + rb.y) + 2 - si.lo + 1;
+    si.lo = ((int)floorf(mn) - 2) & ~7;
+    si.len = (((int)ceilf(mx) + 2 - si.lo + 1) + 7) & ~7;
     si.skip = (si.lo + si.len <= 0 || si.lo > a.ns - 2) ? 1 : 0;
     si.B = (float)(txref + R_r0 - (double)si.lo);
-    si.pad = 0;
+    si.over = si.len > a.W ? si.len : 0;
+    if (si.over) si.len = a.W;
     return si;
 }
 
-template <int MODE, typename T, bool CHECK>
+// Raw samples of one staging segment (8 consecutive samples + the next one)
+// held in registers between the prefetch and the conversion.
+template <typename T> struct Seg;
+template <> struct Seg<int16_t> {
+    uint4 v;
+    int nxt;
+    __device__ __forceinline__ float at(int k, float s) const {
+        const unsigned word = (k >> 1) == 0 ? v.x : (k >> 1) == 1 ? v.y : (k >> 1) == 2 ? v.z : v.w;
+        const int q = (k & 1) ? ((int)word >> 16) : (int)(short)(word & 0xffffu);
+        return (float)q * s;
+    }
+};
+template <> struct Seg<__half> {
+    uint4 v;
+    int nxt;
+    __device__ __forceinline__ float at(int k, float) const {
+        const unsigned word = (k >> 1) == 0 ? v.x : (k >> 1) == 1 ? v.y : (k >> 1) == 2 ? v.z : v.w;
+        return __half2float(__ushort_as_half((unsigned short)((k & 1) ? (word >> 16) : (word & 0xffffu))));
+    }
+};
+template <> struct Seg<float> {
+    float4 v0, v1;
+    int nxt;
+    __device__ __forceinline__ float at(int k, float) const {
+        switch (k) {
+            case 0: return v0.x; case 1: return v0.y; case 2: return v0.z; case 3: return v0.w;
+            case 4: return v1.x; case 5: return v1.y; case 6: return v1.z; default: return v1.w;
+        }
+    }
+};
+
+template <typename T> __device__ __forceinline__ float raw_one(int bits, float s);
+template <> __device__ __forceinline__ float raw_one<int16_t>(int bits, float s) { return (float)(short)bits * s; }
+template <> __device__ __forceinline__ float raw_one<__half>(int bits, float) {
+    return __half2float(__ushort_as_half((unsigned short)bits));
+}
+template <> __device__ __forceinline__ float raw_one<float>(int bits, float) { return __int_as_float(bits); }
+
+template <typename T> __device__ __forceinline__ int raw_bits(const T* p);
+template <> __device__ __forceinline__ int raw_bits<int16_t>(const int16_t* p) { return (int)(unsigned short)__ldg(p); }
+template <> __device__ __forceinline__ int raw_bits<__half>(const __half* p) {
+    return (int)__ldg(reinterpret_cast<const unsigned short*>(p));
+}
+template <> __device__ __forceinline__ int raw_bits<float>(const float* p) { return __float_as_int(__ldg(p)); }
+
+// Load the 8 samples [n0, n0 + 8) of a trace and sample n0 + 8 (zeros outside [0, ns)).
+template <typename T>
+__device__ __forceinline__ void seg_load(Seg<T>& sg, const T* tr, int n0, int ns, bool vec_ok, bool row_ok) {
+    if (!row_ok) {
+        sg = Seg<T>{};
+        sg.nxt = 0;
+        return;
+    }
+    if (vec_ok && n0 >= 0 && n0 + 8 <= ns) {
+        if constexpr (sizeof(T) == 2) {
+            sg.v = __ldg(reinterpret_cast<const uint4*>(tr + n0));
+        } else {
+            sg.v0 = __ldg(reinterpret_cast<const float4*>(tr + n0));
+            sg.v1 = __ldg(reinterpret_cast<const float4*>(tr + n0 + 4));
+        }
+    } else {
+        int b[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) b[k] = (n0 + k >= 0 && n0 + k < ns) ? raw_bits<T>(tr + n0 + k) : 0;
+        if constexpr (sizeof(T) == 2) {
+            sg.v = make_uint4((unsigned)(b[0] & 0xffff) | ((unsigned)b[1] << 16),
+                              (unsigned)(b[2] & 0xffff) | ((unsigned)b[3] << 16),
+                              (unsigned)(b[4] & 0xffff) | ((unsigned)b[5] << 16),
+                              (unsigned)(b[6] & 0xffff) | ((unsigned)b[7] << 16));
+        } else {
+            sg.v0 = make_float4(__int_as_float(b[0]), __int_as_float(b[1]), __int_as_float(b[2]),
+                                __int_as_float(b[3]));
+            sg.v1 = make_float4(__int_as_float(b[4]), __int_as_float(b[5]), __int_as_float(b[6]),
+                                __int_as_float(b[7]));
+        }
+    }
+    sg.nxt = (n0 + 8 >= 0 && n0 + 8 < ns) ? raw_bits<T>(tr + n0 + 8) : 0;
+}
+
+// Convert a segment to 8 FP32 pairs (x[n], x[n+1] - x[n]); pairs whose n is
+// outside [0, ns - 2] are zero (no recorded neighbour).
+template <typename T>
+__device__ __forceinline__ void seg_store(const Seg<T>& sg, float2* dst, int n0, int ns, float scale) {
+    float v[9];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = sg.at(k, scale);
+    v[8] = raw_one<T>(sg.nxt, scale);
+    float4 o[4];
+    const bool full = n0 >= 0 && n0 + 8 <= ns - 1;
+#pragma unroll
+    for (int k = 0; k < 8; k += 2) {
+        float2 p0 = make_float2(v[k], v[k + 1] - v[k]);
+        float2 p1 = make_float2(v[k + 1], v[k + 2] - v[k + 1]);
+        if (!full) {
+            if (!(n0 + k >= 0 && n0 + k <= ns - 2)) p0 = make_float2(0.0f, 0.0f);
+            if (!(n0 + k + 1 >= 0 && n0 + k + 1 <= ns - 2)) p1 = make_float2(0.0f, 0.0f);
+        }
+        o[k >> 1] = make_float4(p0.x, p0.y, p1.x, p1.y);
+    }
+    float4* d4 = reinterpret_cast<float4*>(dst);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) d4[k] = o[k];
+}
+
+template <typename T, int P>
+__device__ __forceinline__ void stage_prefetch(Seg<T> (&sg)[2], const DasArgs& a, const T* rf,
+                                               const StageInfo& si, int t, int r0, int r_last,
+                                               bool vec_ok) {
+    const int nseg = si.len >> 3;
+    const float inv = 1.0f / (float)nseg;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int gidx = threadIdx.x + i * kThreads;
+        if (gidx < kC * nseg) {
+            const int c = (int)(((float)gidx + 0.5f) * inv);
+            const int k = gidx - c * nseg;
+            const int r = r0 + c;
+            const T* tr = rf + ((long long)t * a.g.n_elements + min(r, a.g.n_elements - 1)) * a.ns;
+            seg_load<T>(sg[i], tr, si.lo + 8 * k, a.ns, vec_ok, r <= r_last);
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void stage_store(const Seg<T> (&sg)[2], float2* buf, const DasArgs& a,
+                                            const StageInfo& si) {
+    const int nseg = si.len >> 3;
+    const float inv = 1.0f / (float)nseg;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int gidx = threadIdx.x + i * kThreads;
+        if (gidx < kC * nseg) {
+            const int c = (int)(((float)gidx + 0.5f) * inv);
+            const int k = gidx - c * nseg;
+            seg_store<T>(sg[i], buf + c * a.W + 8 * k, si.lo + 8 * k, a.ns, a.rf_scale);
+        }
+    }
+}
+
+__device__ __forceinline__ float warp_min(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Window of stage (slice transmit j, chunk starting at r0), computed by one
+// warp: lane c (mod 8) bounds receive element r0 + c, then min/max over lanes.
+template <int MODE>
+__device__ __forceinline__ StageInfo warp_stage_info(const DasArgs& a, const TileGeo& tg,
+                                                     const TxInfo& ti, double txref, int r0,
+                                                     int r_last, double R_r0) {
+    const int r = min(r0 + (threadIdx.x & 7), r_last);
+    const float2 bd = pair_bounds<MODE>(a.g, ti, r, tg.xlo, tg.xhi, tg.zlo, tg.zhi);
+    return make_stage(a, warp_min(bd.x), warp_max(bd.y), txref, R_r0);
+}
+
+template <int MODE, typename T, int P, bool CHECK>
 __global__ void __launch_bounds__(kThreads, 2) das_tiled_kernel(const __grid_constant__ DasArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2* buf = reinterpret_cast<float2*>(smem_raw);                  // [kC][W]
-    float2* ttab = buf + kC * a.W;                                       // [kTS][kP][kThreads]
-    Elem* el = reinterpret_cast<Elem*>(ttab + kTS * kP * kThreads);      // [E]
-    __shared__ float2 s_tb[kTS];
+    float2* buf = reinterpret_cast<float2*>(smem_raw);                  // [kC][W] sample pairs
+    float2* ttab = buf + kC * a.W;                                       // [kTS][P][kThreads]
+    Elem* el = reinterpret_cast<Elem*>(ttab + kTS * P * kThreads);       // [E]
     __shared__ double s_txref[kTS];
+    __shared__ float2 s_dtw[kTS][kThreads / 32];   // per-warp min/max transmit correction
     __shared__ int s_tlist[kTS];
     __shared__ int s_nact;
     __shared__ StageInfo s_si[2];
 
     const Geom& g = a.g;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int lx = lane & 3, lz = lane >> 2;
     const int item = blockIdx.x, b = blockIdx.y;
     const int slice = item % a.n_slices, tile = item / a.n_slices;
-    const TileGeo tg = tile_geo(a, (tile % a.tiles_x) * kTX, (tile / a.tiles_x) * kTZ);
+    const TileGeo tg = tile_geo<P>(a, (tile % a.tiles_x) * kTX, (tile / a.tiles_x) * (8 * P));
     const T* rf = reinterpret_cast<const T*>(a.rf) + (long long)b * a.frame_elems;
+    const bool vec_ok = (a.ns & 7) == 0;
 
-    // Pixel offsets from the reference point; FP32 depths for the aperture.
-    const float ux = (float)lane * g.gdx;
-    float uz[kP], kz[kP], kap[kP];
+    // Pixel offsets from the reference point: column 4 warp + lx, rows lz + 8 p.
+    const int col = 4 * warp + lx;
+    const float ux = (float)col * g.gdx;
+    float kz[P], kap[P], uz[P];
 #pragma unroll
-    for (int p = 0; p < kP; ++p) {
-        uz[p] = (float)(warp * kP + p) * g.gdz;
+    for (int p = 0; p < P; ++p) {
+        uz[p] = (float)(lz + 8 * p) * g.gdz;
         kz[p] = uz[p] * fmaf(2.0f, (float)tg.cz, uz[p]);
         kap[p] = aperture_kappa(g, (float)tg.cz + uz[p]);
     }
+    // Elements that can weigh on this warp's 4 columns (all rows of the tile).
+    const int2 wr = tile_elements(g, pixel_x(g, tg.ix0 + 4 * warp), pixel_x(g, tg.ix0 + 4 * warp + 3),
+                                  tg.zhi);
 
     const int t_begin = slice * kTS, t_end = min(a.n_tx, t_begin + kTS);
     const int2 er = tg.er;
@@ -290,11 +460,13 @@ __global__ void __launch_bounds__(kThreads, 2) das_tiled_kernel(const __grid_con
     __syncthreads();
     const int n_act = s_nact;
 
-    // Transmit terms of the slice: FP64 reference, FP32 per-pixel correction + weight.
+    // Transmit terms of the slice: FP32 per-pixel correction + weight (thread-private table),
+    // FP64 reference per transmit, per-warp range of the corrections.
     for (int j = 0; j < n_act; ++j) {
         const TxInfo& ti = a.tx[s_tlist[j]];
+        float mn = 3.0e38f, mx = -3.0e38f;
 #pragma unroll
-        for (int p = 0; p < kP; ++p) {
+        for (int p = 0; p < P; ++p) {
             float2 v;
             if (MODE == 0) {
                 const Elem et = el[ti.e - er.x];
@@ -304,97 +476,129 @@ __global__ void __launch_bounds__(kThreads, 2) das_tiled_kernel(const __grid_con
                 v.x = fmaf(ux, ti.sin_f, uz[p] * ti.cos_f);
                 v.y = 1.0f;
             }
-            ttab[(j * kP + p) * kThreads + tid] = v;
+            mn = fminf(mn, v.x);
+            mx = fmaxf(mx, v.x);
+            ttab[(j * P + p) * kThreads + tid] = v;
         }
-        if (tid == j) {
-            s_tb[j] = tx_bounds<MODE>(g, ti, tg.xlo, tg.xhi, tg.zlo, tg.zhi);
-            s_txref[j] = tx_ref<MODE>(ti, tg.cx, tg.cz, MODE == 0 ? el[ti.e - er.x].R : 0.0);
-        }
+        mn = warp_min(mn);
+        mx = warp_max(mx);
+        if (lane == 0) s_dtw[j][warp] = make_float2(mn, mx);
+        if (tid == j) s_txref[j] = tx_ref<MODE>(ti, tg.cx, tg.cz, MODE == 0 ? el[ti.e - er.x].R : 0.0);
     }
     const int n_chunks = n_act > 0 ? (er.y - er.x + kC) / kC : 0;
     const int n_stages = n_chunks * n_act;
     __syncthreads();
-    if (tid == 0 && n_stages > 0) {
-        const int r_last = min(er.x + kC - 1, er.y);
-        s_si[0] = stage_info(a, tg, s_tb[0], s_txref[0], er.x, r_last, el[0].R);
+
+    float acc[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) acc[p] = 0.0f;
+    float Dr[kC][P], Wr[kC][P];
+    float dr_min = 0.0f, dr_max = 0.0f;
+    unsigned cmask = 0u;
+    Seg<T> sg[2];
+
+    // Stage infos are computed by warp 0 two stages ahead (double-buffered in
+    // shared memory); every thread prefetches its raw samples one stage ahead.
+    auto stage_of = [&](int qq, int& jj, int& rr0, int& rrl) {
+        const int kk = qq / n_act;
+        jj = qq - kk * n_act;
+        rr0 = er.x + kk * kC;
+        rrl = min(rr0 + kC - 1, er.y);
+    };
+    auto info_for = [&](int qq) {
+        int jj, rr0, rrl;
+        stage_of(qq, jj, rr0, rrl);
+        return warp_stage_info<MODE>(a, tg, a.tx[s_tlist[jj]], s_txref[jj], rr0, rrl,
+                                     el[rr0 - er.x].R);
+    };
+    if (n_stages > 0) {
+        if (warp == 0) {
+            const StageInfo s0 = info_for(0);
+            if (lane == 0) s_si[0] = s0;
+        }
+        __syncthreads();
+        const StageInfo s0 = s_si[0];
+        if (!s0.skip) stage_prefetch<T, P>(sg, a, rf, s0, s_tlist[0], er.x, min(er.x + kC - 1, er.y), vec_ok);
+        if (warp == 0 && n_stages > 1) {
+            const StageInfo s1 = info_for(1);
+            if (lane == 0) s_si[1] = s1;
+        }
     }
 
-    float acc[kP];
-#pragma unroll
-    for (int p = 0; p < kP; ++p) acc[p] = 0.0f;
-    float Dr[kC][kP], Wr[kC][kP];
-    __syncthreads();
-
     for (int q = 0; q < n_stages; ++q) {
-        const int k = q / n_act, j = q - k * n_act;
-        const int r0 = er.x + k * kC;
-        const int r_last = min(r0 + kC - 1, er.y);
+        int j, r0, r_last;
+        stage_of(q, j, r0, r_last);
+        const StageInfo si = s_si[q & 1];
+        const int t = s_tlist[j];
+        if (si.over && tid == 0) flag(a.hdr, 1u, (unsigned)blockIdx.x, (unsigned)si.over, (unsigned)a.W);
+        if (!si.skip) stage_store<T>(sg, buf, a, si);
+        __syncthreads();   // pairs of stage q visible; info of stage q + 1 visible
+        if (q + 1 < n_stages) {
+            int j1, r01, rl1;
+            stage_of(q + 1, j1, r01, rl1);
+            const StageInfo s1 = s_si[(q + 1) & 1];
+            if (!s1.skip) stage_prefetch<T, P>(sg, a, rf, s1, s_tlist[j1], r01, rl1, vec_ok);
+        }
+        if (warp == 0 && q + 2 < n_stages) {
+            const StageInfo s2 = info_for(q + 2);
+            if (lane == 0) s_si[q & 1] = s2;
+        }
         if (j == 0) {
-            // Receive chunk: window-relative distances C_c + delta and weights in registers.
+            // Receive chunk: window-relative distances C_c + delta and weights in registers;
+            // the warp's active elements and range of the receive term.
             const double R0 = el[r0 - er.x].R;
+            cmask = 0u;
+            float mn = 3.0e38f, mx = -3.0e38f;
 #pragma unroll
             for (int c = 0; c < kC; ++c) {
                 const int re = min(r0 + c, r_last);  // padding reuses the last element, weight 0
                 const Elem ee = el[re - er.x];
                 const float cc = (float)(ee.R - R0);
+                const bool on = r0 + c <= r_last && r0 + c >= wr.x && r0 + c <= wr.y;
+                if (on) cmask |= 1u << c;
 #pragma unroll
-                for (int p = 0; p < kP; ++p) {
+                for (int p = 0; p < P; ++p) {
                     Dr[c][p] = cc + dist_delta(ee, ux, kz[p]);
-                    Wr[c][p] = (r0 + c <= r_last) ? apod_w(g.apod, -(ee.ax + ux), kap[p]) * ee.g
-                                                  : 0.0f;
+                    Wr[c][p] = on ? apod_w(g.apod, -(ee.ax + ux), kap[p]) * ee.g : 0.0f;
+                    if (on) {
+                        mn = fminf(mn, Dr[c][p]);
+                        mx = fmaxf(mx, Dr[c][p]);
+                    }
                 }
             }
+            dr_min = warp_min(mn);
+            dr_max = warp_max(mx);
         }
-        const StageInfo si = s_si[q & 1];
-        const int t = s_tlist[j];
-        int len = si.len;
-        if (!si.skip) {
-            if (len > a.W) {
-                if (tid == 0) flag(a.hdr, 1u, (unsigned)blockIdx.x, (unsigned)len, (unsigned)a.W);
-                len = a.W;
-            }
-            // Stage the window of the kC traces (t, r0..r0+kC-1) as FP32 pairs.
-#pragma unroll 1
-            for (int c = 0; c < kC; ++c) {
-                const int r = r0 + c;
-                float2* dst = buf + c * a.W;
-                const T* tr = rf + ((long long)t * g.n_elements + r) * a.ns;
-                const bool ok_r = r <= r_last;
-                for (int qq = tid; qq < len; qq += kThreads) {
-                    const int n = si.lo + qq;
-                    float2 v = make_float2(0.0f, 0.0f);
-                    if (ok_r && n >= 0 && n <= a.ns - 2) v = RF<T>::pair(tr + n, a.rf_scale);
-                    dst[qq] = v;
-                }
-            }
+        // Warp-level skip: transmit or chunk outside this warp's aperture, or every
+        // delay of the warp outside the record.
+        bool live = !si.skip && cmask != 0u;
+        if (MODE == 0) live = live && a.tx[t].e >= wr.x && a.tx[t].e <= wr.y;
+        if (live) {
+            const float2 dtw = s_dtw[j][warp];
+            const float lo_f = (float)si.lo + si.B;
+            live = (lo_f + dtw.x + dr_min <= (float)(a.ns - 1) + 0.5f) && (lo_f + dtw.y + dr_max >= -0.5f);
         }
-        if (tid == 0 && q + 1 < n_stages) {
-            const int k1 = (q + 1) / n_act, j1 = (q + 1) - k1 * n_act;
-            const int r01 = er.x + k1 * kC;
-            s_si[(q + 1) & 1] = stage_info(a, tg, s_tb[j1], s_txref[j1], r01,
-                                           min(r01 + kC - 1, er.y), el[r01 - er.x].R);
-        }
-        __syncthreads();
-        if (!si.skip) {
-            float tw[kP], wt[kP], acct[kP];
+        if (live) {
+            float tw[P], wt[P], acct[P];
 #pragma unroll
-            for (int p = 0; p < kP; ++p) {
-                const float2 v = ttab[(j * kP + p) * kThreads + tid];
+            for (int p = 0; p < P; ++p) {
+                const float2 v = ttab[(j * P + p) * kThreads + tid];
                 tw[p] = si.B + v.x;
                 wt[p] = v.y;
                 acct[p] = 0.0f;
             }
 #pragma unroll
             for (int c = 0; c < kC; ++c) {
+                if (!(cmask & (1u << c))) continue;
                 const float2* bc = buf + c * a.W;
 #pragma unroll
-                for (int p = 0; p < kP; ++p) {
+                for (int p = 0; p < P; ++p) {
                     const float s = tw[p] + Dr[c][p];
                     const float m = __fadd_rd(s, kMagic);
                     const float f = s - (m - kMagic);
                     int idx = __float_as_int(m) - kMagicBits;
-                    if (CHECK && (idx < 0 || idx >= len)) {
-                        flag(a.hdr, 2u, (unsigned)blockIdx.x, (unsigned)idx, (unsigned)len);
+                    if (CHECK && (idx < 0 || idx >= si.len || idx >= a.W)) {
+                        flag(a.hdr, 2u, (unsigned)blockIdx.x, (unsigned)idx, (unsigned)si.len);
                         idx = 0;
                     }
                     const float2 ab = bc[idx];
@@ -402,28 +606,32 @@ __global__ void __launch_bounds__(kThreads, 2) das_tiled_kernel(const __grid_con
                 }
             }
 #pragma unroll
-            for (int p = 0; p < kP; ++p) acc[p] = fmaf(wt[p], acct[p], acc[p]);
+            for (int p = 0; p < P; ++p) acc[p] = fmaf(wt[p], acct[p], acc[p]);
         }
-        __syncthreads();
+        __syncthreads();   // compute of stage q done before stage q + 1 overwrites the pairs
     }
 
-    float* dst = a.part + ((long long)b * a.n_items + item) * kTilePix;
+    // Partial tile in thread order: [p][tid].
+    float* dst = a.part + ((long long)b * a.n_items + item) * (kThreads * P);
 #pragma unroll
-    for (int p = 0; p < kP; ++p) dst[(warp * kP + p) * kTX + lane] = acc[p];
+    for (int p = 0; p < P; ++p) dst[p * kThreads + tid] = acc[p];
 }
 
 // Sum the transmit-slice partials of every pixel in slice order.
+template <int P>
 __global__ void das_reduce_kernel(const float* __restrict__ part, float* __restrict__ out, int nz,
                                   int nx, int tiles_x, int n_slices, int n_items) {
     const int ix = blockIdx.x * blockDim.x + threadIdx.x;
     const int iz = blockIdx.y;
     const int b = blockIdx.z;
     if (ix >= nx) return;
-    const int tile = (iz / kTZ) * tiles_x + ix / kTX;
-    const int local = (iz % kTZ) * kTX + (ix % kTX);
-    const float* p = part + ((long long)b * n_items + (long long)tile * n_slices) * kTilePix + local;
+    const int tile = (iz / (8 * P)) * tiles_x + ix / kTX;
+    const int cl = ix % kTX, rl = iz % (8 * P);
+    const int tid = (cl >> 2) * 32 + (rl & 7) * 4 + (cl & 3);
+    const int local = (rl >> 3) * kThreads + tid;
+    const float* p = part + ((long long)b * n_items + (long long)tile * n_slices) * (kThreads * P) + local;
     float s = 0.0f;
-    for (int k = 0; k < n_slices; ++k) s += p[(long long)k * kTilePix];
+    for (int k = 0; k < n_slices; ++k) s += p[(long long)k * (kThreads * P)];
     out[((long long)b * nz + iz) * nx + ix] = s;
 }
 
@@ -480,7 +688,7 @@ __global__ void __launch_bounds__(256) das_direct_kernel(const __grid_constant__
 // plus the FP32 window-relative value, for (pixel, transmit, element) triples.
 // Triples the kernel never evaluates (element outside the tile's aperture
 // range, inactive transmit) are NaN.
-template <int MODE>
+template <int MODE, int P>
 __global__ void das_delays_kernel(const __grid_constant__ DasArgs a, const int32_t* __restrict__ pix,
                                   int n_pix, double* __restrict__ out) {
     const Geom& g = a.g;
@@ -492,7 +700,7 @@ __global__ void das_delays_kernel(const __grid_constant__ DasArgs a, const int32
         const int q = (int)(i / ((long long)g.n_elements * a.n_tx));
         const int lin = pix[q];
         const int ix = lin % g.nx, iz = lin / g.nx;
-        const TileGeo tg = tile_geo(a, (ix / kTX) * kTX, (iz / kTZ) * kTZ);
+        const TileGeo tg = tile_geo<P>(a, (ix / kTX) * kTX, (iz / (8 * P)) * (8 * P));
         const TxInfo& ti = a.tx[t];
         const int2 er = tg.er;
         if (r < er.x || r > er.y || (MODE == 0 && (ti.e < er.x || ti.e > er.y))) {
@@ -515,9 +723,13 @@ __global__ void das_delays_kernel(const __grid_constant__ DasArgs a, const int32
         } else {
             dtx = fmaf(ux, ti.sin_f, uz * ti.cos_f);
         }
-        const float2 tb = tx_bounds<MODE>(g, ti, tg.xlo, tg.xhi, tg.zlo, tg.zhi);
-        const StageInfo si = stage_info(a, tg, tb, tx_ref<MODE>(ti, tg.cx, tg.cz, R_et), r0, r_last,
-                                        e0.R);
+        float mn = 3.0e38f, mx = -3.0e38f;
+        for (int rr = r0; rr <= r_last; ++rr) {
+            const float2 bd = pair_bounds<MODE>(g, ti, rr, tg.xlo, tg.xhi, tg.zlo, tg.zhi);
+            mn = fminf(mn, bd.x);
+            mx = fmaxf(mx, bd.y);
+        }
+        const StageInfo si = make_stage(a, mn, mx, tx_ref<MODE>(ti, tg.cx, tg.cz, R_et), e0.R);
         const float dr = (float)(erl.R - e0.R) + dist_delta(erl, ux, kz);
         const float s = (si.B + dtx) + dr;
         out[i] = (double)si.lo + (double)s;
@@ -580,43 +792,64 @@ double max_delay(const wf_probe* p, const wf_grid* g) {
 
 struct Plan {
     int tiles_x, tiles_z, n_slices, n_items;
-    int W;
+    int W, P;
     bool tiled;
     size_t smem;
     size_t ws_bytes;
 };
+
+// Upper bound on one staging window for a tile of kTX x 8P pixels: both
+// distance terms move by at most the tile diagonal, the receive term by
+// (kC - 1) pitches across the chunk; plus floor/ceil, the +-2 margins and the
+// 8-sample alignment of both ends.
+int window_bound(const GeomD& D, int P) {
+    const double ex = (double)(kTX - 1) * D.gdx, ez = (double)(8 * P - 1) * D.gdz;
+    const double diam = std::sqrt(ex * ex + ez * ez);
+    const double w = 2.0 * diam + (kC - 1) * D.pitch + 24.0;
+    return (int)std::ceil(w / 8.0) * 8;
+}
 
 Plan make_plan(const wf_probe* p, const wf_grid* g, int batch, int n_tx) {
     Geom G;
     GeomD D;
     make_geom(p, g, G, D);
     Plan P;
+    P.P = window_bound(D, 4) <= kMaxWindow ? 4 : 2;
+    P.W = window_bound(D, P.P);
+    P.tiled = P.W <= kMaxWindow;
     P.tiles_x = (g->nx + kTX - 1) / kTX;
-    P.tiles_z = (g->nz + kTZ - 1) / kTZ;
+    P.tiles_z = (g->nz + 8 * P.P - 1) / (8 * P.P);
     P.n_slices = (n_tx + kTS - 1) / kTS;
     P.n_items = P.tiles_x * P.tiles_z * P.n_slices;
-    // Lipschitz bound on one staging window: both distance terms move by at
-    // most the tile diagonal, the receive term by (kC-1) pitches across the
-    // chunk; plus floor/ceil and the +-2 margins.
-    const double ex = (double)(kTX - 1) * D.gdx, ez = (double)(kTZ - 1) * D.gdz;
-    const double diam = std::sqrt(ex * ex + ez * ez);
-    const double w = 2.0 * diam + (kC - 1) * D.pitch + 16.0;
-    P.W = (int)std::ceil(w / 4.0) * 4;
-    P.tiled = P.W <= kMaxWindow;
-    P.smem = (size_t)kC * P.W * sizeof(float2) + (size_t)kTS * kP * kThreads * sizeof(float2) +
+    P.smem = (size_t)kC * P.W * sizeof(float2) + (size_t)kTS * P.P * kThreads * sizeof(float2) +
              (size_t)p->n_elements * sizeof(Elem);
     P.ws_bytes = kWsHeaderBytes +
-                 (P.tiled ? (size_t)batch * P.n_items * kTilePix * sizeof(float) : 0);
+                 (P.tiled ? (size_t)batch * P.n_items * kThreads * P.P * sizeof(float) : 0);
     return P;
 }
 
 constexpr size_t kMaxTiledSmem = (size_t)kC * kMaxWindow * sizeof(float2) +
-                                  (size_t)kTS * kP * kThreads * sizeof(float2) +
+                                  (size_t)kTS * 4 * kThreads * sizeof(float2) +
                                   (size_t)WF_MAX_ELEMENTS * sizeof(Elem);
 
 bool check_bounds_mode() {
     const char* v = std::getenv("WF_CHECK_BOUNDS");
     return v && v[0] && v[0] != '0';
+}
+
+template <int MODE, typename T, int P>
+wf_status launch_tiled(DasArgs& A, const Plan& PL, int batch, cudaStream_t st) {
+    static unsigned long long smem_set[2] = {0ull, 0ull};
+    const bool chk = check_bounds_mode();
+    auto kern = chk ? das_tiled_kernel<MODE, T, P, true> : das_tiled_kernel<MODE, T, P, false>;
+    wf_status s = ensure_smem_limit(kern, kMaxTiledSmem, smem_set[chk ? 1 : 0]);
+    if (s != WF_OK) return s;
+    kern<<<dim3(PL.n_items, batch), kThreads, PL.smem, st>>>(A);
+    if ((s = last_launch_status()) != WF_OK) return s;
+    dim3 rg((A.g.nx + 127) / 128, A.g.nz, batch);
+    das_reduce_kernel<P><<<rg, 128, 0, st>>>(A.part, A.out, A.g.nz, A.g.nx, PL.tiles_x, PL.n_slices,
+                                             PL.n_items);
+    return last_launch_status();
 }
 
 template <int MODE, typename T>
@@ -626,17 +859,7 @@ wf_status launch_das(DasArgs& A, const Plan& P, int batch, cudaStream_t st) {
         das_direct_kernel<MODE, T><<<grid, 256, 0, st>>>(A);
         return last_launch_status();
     }
-    static unsigned long long smem_set[2] = {0ull, 0ull};
-    const bool chk = check_bounds_mode();
-    auto kern = chk ? das_tiled_kernel<MODE, T, true> : das_tiled_kernel<MODE, T, false>;
-    wf_status s = ensure_smem_limit(kern, kMaxTiledSmem, smem_set[chk ? 1 : 0]);
-    if (s != WF_OK) return s;
-    kern<<<dim3(P.n_items, batch), kThreads, P.smem, st>>>(A);
-    if ((s = last_launch_status()) != WF_OK) return s;
-    dim3 rg((A.g.nx + 127) / 128, A.g.nz, batch);
-    das_reduce_kernel<<<rg, 128, 0, st>>>(A.part, A.out, A.g.nz, A.g.nx, P.tiles_x, P.n_slices,
-                                          P.n_items);
-    return last_launch_status();
+    return P.P == 4 ? launch_tiled<MODE, T, 4>(A, P, batch, st) : launch_tiled<MODE, T, 2>(A, P, batch, st);
 }
 
 template <int MODE>
@@ -674,6 +897,7 @@ wf_status das_common(int mode, const wf_probe* probe, const wf_grid* grid, int32
     A.n_slices = P.n_slices;
     A.n_items = P.n_items;
     A.W = P.W;
+    A.P = P.P;
     A.rf = rf;
     A.rf_scale = dtype == WF_I16 ? rf_scale : 1.0f;
     A.frame_elems = (long long)n_tx * probe->n_elements * n_samples;
@@ -772,9 +996,18 @@ extern "C" wf_status wf_das_delays(const wf_probe* probe, const wf_grid* grid, i
     if (n_pix == 0) return WF_OK;
     make_geom(probe, grid, a.g, a.gd);
     a.n_tx = n_tx;
+    a.ns = 1 << 30;  // the probe reports delays regardless of the record length
+    const Plan P = make_plan(probe, grid, 1, n_tx);
+    a.W = P.W;
+    a.P = P.P;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    if (mode == 0) das_delays_kernel<0><<<304, 256, 0, st>>>(a, pix, n_pix, out);
-    else das_delays_kernel<1><<<304, 256, 0, st>>>(a, pix, n_pix, out);
+    if (mode == 0) {
+        if (P.P == 4) das_delays_kernel<0, 4><<<304, 256, 0, st>>>(a, pix, n_pix, out);
+        else das_delays_kernel<0, 2><<<304, 256, 0, st>>>(a, pix, n_pix, out);
+    } else {
+        if (P.P == 4) das_delays_kernel<1, 4><<<304, 256, 0, st>>>(a, pix, n_pix, out);
+        else das_delays_kernel<1, 2><<<304, 256, 0, st>>>(a, pix, n_pix, out);
+    }
     return last_launch_status();
 }
 
