@@ -6,39 +6,48 @@
 //   both: Dr = |p - x_r|,                     Wr = apod(p, r) g_r
 // (all lengths in samples).  DAS is a gather-sum, not a contraction: no
 // tensor cores.  Design (GB300):
-//  * a CTA owns a 16 (z) x 32 (x) pixel tile and one slice of transmits; the
-//    tile's aperture gives the range of elements that can contribute;
-//  * geometry is tile-relative: each CTA takes its tile origin c as reference
-//    and, per element, the exact distance R_e = |c - x_e| in FP64; a pixel at
-//    c + u then needs only the small FP32 correction
+//  * a CTA (8 warps) owns a pixel tile and one slice of transmits.  A warp
+//    covers WCOL columns; its lanes (and P pixels per lane) run down the rows.
+//    STAI uses one column per warp (tile 8 x 64): a transmit/receive pair is
+//    live for whole columns, so all warps of a tile share the same aperture.
+//    PWI uses 4 columns per warp (tile 32 x 32): its plane-wave delays vary
+//    slowly across x, so wide tiles reuse each staged sample more.
+//  * geometry is tile-relative: the tile origin c is the reference point and
+//    R_e = |c - x_e| is exact (FP64, stored as a float hi/lo pair); a pixel at
+//    c + u needs only the small FP32 correction
 //      delta = |c + u - x_e| - R_e = N / (R_e + |c + u - x_e|),
 //      N = u_x (2 (c_x - x_e) + u_x) + u_z (2 c_z + u_z),
 //    and every fractional delay is formed relative to its staging window, so
 //    FP32 carries a few hundred samples of range instead of thousands (delay
 //    error ~3e-5 samples instead of ~2e-4);
-//  * receive elements are processed in chunks of 8 whose corrections and
-//    weights live in registers; transmit corrections of the slice sit in a
-//    thread-private shared table; nothing geometric is read from global memory;
+//  * receive elements are processed in chunks of 8: corrections and weights in
+//    registers, computed only by warps with an element of the chunk in their
+//    aperture; STAI transmit corrections of the slice sit in a thread-private
+//    shared table; nothing geometric is read from global memory;
 //  * for every (transmit, receive chunk) the sample window the tile can touch
-//    is staged into shared memory as FP32 pairs (x[i], x[i+1]-x[i]), so one
-//    8-byte shared load and one FMA interpolate a sample;
+//    (exact convex bounds of the delay over the tile) is staged into shared
+//    memory as FP32 pairs (x[i], x[i+1]-x[i]): one 8-byte shared load and one
+//    FMA interpolate a sample.  Raw samples are loaded 16 bytes at a time one
+//    stage ahead; the int16 scale is folded into the receive weights;
+//  * warps skip stages whose transmit or receive chunk lies outside their
+//    aperture or whose delays all fall outside the record;
 //  * the floor of the window-relative delay is a round-down add of 1.5 * 2^23;
 //  * partial images of the transmit slices go to the workspace and a second
 //    kernel sums them in slice order (deterministic).
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
+#include <cstdio>
 #include <cstring>
 
 #include "common.cuh"
 
 namespace wf {
 
-constexpr int kTX = 32;                    // tile columns (x): 8 warps x 4 columns
-constexpr int kThreads = 256;              // 8 warps; lane = (row 0..7) * 4 + (column 0..3)
+constexpr int kThreads = 256;              // 8 warps
 constexpr int kC = 8;                      // receive elements per chunk
-constexpr int kTS = 8;                     // transmits per slice
-constexpr int kMaxWindow = 512;            // staged positions per trace (2 segments/thread)
+constexpr int kTS = 16;                    // transmits (or angles) per slice
+constexpr int kMaxWindow = 512;            // staged positions per trace: 64 segments of 8
 constexpr float kMagic = 12582912.0f;      // 1.5 * 2^23
 constexpr int kMagicBits = 0x4B400000;
 
@@ -60,34 +69,22 @@ struct DasArgs {
     int n_tx, ns;
     int tiles_x, n_slices, n_items;  // items per frame = tiles * slices
     int W;                           // staged positions per trace (shared stride)
-    int P;                           // tile rows / 8 (pixels per thread)
+    int ring;                        // TMA raw-sample ring depth
     const void* rf;
     float rf_scale;
     long long frame_elems;           // n_tx * E * ns
     float* part;                     // [batch][n_items][256 * P] slice partials
-    float* out;                      // direct kernel only
+    float* out;
     WsHeader* hdr;
     TxInfo tx[WF_MAX_TX];
 };
 
-template <typename T> struct RF;
-template <> struct RF<float> {
-    static __device__ __forceinline__ float2 pair(const float* p, float) {
-        float a = __ldg(p), b = __ldg(p + 1);
-        return make_float2(a, b - a);
-    }
-};
-template <> struct RF<__half> {
-    static __device__ __forceinline__ float2 pair(const __half* p, float) {
-        float a = __half2float(p[0]), b = __half2float(p[1]);
-        return make_float2(a, b - a);
-    }
-};
-template <> struct RF<int16_t> {
-    static __device__ __forceinline__ float2 pair(const int16_t* p, float s) {
-        int a = __ldg(p), b = __ldg(p + 1);
-        return make_float2((float)a * s, (float)(b - a) * s);
-    }
+// Tile shape of a kernel configuration.
+template <int WCOL, int P>
+struct Shape {
+    static constexpr int kLR = 32 / WCOL;     // lane rows per warp
+    static constexpr int kCols = 8 * WCOL;    // tile columns
+    static constexpr int kRows = kLR * P;     // tile rows
 };
 
 // Hann window 0.5 (1 + cos(pi u)) for |u| < 1, as the Taylor series of the
@@ -114,14 +111,13 @@ __device__ __forceinline__ float apod_w(int apod, float dxe, float kap) {
     return apod == WF_APOD_RECT ? 1.0f : hann_poly(u);
 }
 
-// Per-element reference data of a tile (shared memory).
+// Per-element reference data of a tile (shared memory): R_e = Rhi + Rlo exactly
+// enough (FP64 split into two floats), c_x - x_e and the element weight.
 struct Elem {
-    double R;   // |c - x_e|, samples, FP64
-    float ax;   // c_x - x_e
-    float Rf;   // (float) R
-    float g;    // per-element weight
-    float pad;
+    float Rhi, Rlo, ax, g;
 };
+
+__device__ __forceinline__ double elem_R(const Elem& e) { return (double)e.Rhi + (double)e.Rlo; }
 
 // Exact-to-FP64 distance from the reference point to element e.
 __device__ __forceinline__ Elem make_elem(const DasArgs& a, double cx, double cz, int e) {
@@ -130,26 +126,31 @@ __device__ __forceinline__ Elem make_elem(const DasArgs& a, double cx, double cz
     const double r2 = fma(ax, ax, cz * cz);
     const float rf = sqrtf((float)r2);
     // one Newton step on top of the FP32 root: error ~1e-14 relative
-    const double R = (double)rf + (double)((float)fma(-(double)rf, (double)rf, r2) * (0.5f / rf));
+    double R = (double)rf + (double)((float)fma(-(double)rf, (double)rf, r2) * (0.5f / rf));
+    if (!(r2 > 0.0)) R = 0.0;
     Elem el;
-    el.R = r2 > 0.0 ? R : 0.0;
+    el.Rhi = (float)R;
+    el.Rlo = (float)(R - (double)el.Rhi);
     el.ax = (float)ax;
-    el.Rf = (float)el.R;
     el.g = a.g.elem_weight ? __ldg(a.g.elem_weight + e) : 1.0f;
-    el.pad = 0.0f;
     return el;
 }
 
 // FP32 correction |c + u - x_e| - R_e for a pixel at offset (ux, uz); kz = uz (2 cz + uz).
 __device__ __forceinline__ float dist_delta(const Elem& el, float ux, float kz) {
     const float n = fmaf(ux, 2.0f * el.ax + ux, kz);
-    const float t = fmaf(el.Rf, el.Rf, n);
+    const float t = fmaf(el.Rhi, el.Rhi, n);
     const float d = t > 0.0f ? t * rsqrtf(t) : 0.0f;
-    const float den = el.Rf + d;
+    const float den = el.Rhi + d;
     return den > 0.0f ? __fdividef(n, den) : 0.0f;
 }
 
-// Element range that can be inside the aperture of some pixel of the tile.
+// R_e - R_ref of two elements of the same tile, in FP32 (the hi parts differ exactly).
+__device__ __forceinline__ float elem_rel(const Elem& e, const Elem& ref) {
+    return (e.Rhi - ref.Rhi) + (e.Rlo - ref.Rlo);
+}
+
+// Element range that can be inside the aperture of some pixel of [xlo, xhi] x [.., zhi].
 __device__ __forceinline__ int2 tile_elements(const Geom& g, float xlo, float xhi, float zhi) {
     if (g.apod == WF_APOD_NONE) return make_int2(0, g.n_elements - 1);
     if (!(zhi > 0.0f)) return make_int2(1, 0);
@@ -204,16 +205,16 @@ __device__ __forceinline__ void flag(WsHeader* h, unsigned bit, unsigned a, unsi
     }
 }
 
-// Tile geometry shared by the DAS kernel and the delay probe.  A tile is
-// kTX columns by 8 P rows; its origin pixel is the FP64 reference point.
+// Tile geometry shared by the DAS kernel and the delay probe; the origin pixel
+// of the tile is the FP64 reference point.
 struct TileGeo {
     int ix0, iz0;
-    double cx, cz;            // reference point (FP64 samples)
-    float xlo, xhi, zlo, zhi; // tile rectangle (FP32 samples)
-    int2 er;                  // element range
+    double cx, cz;
+    float xlo, xhi, zlo, zhi;
+    int2 er;
 };
 
-template <int P>
+template <int COLS, int ROWS>
 __device__ __forceinline__ TileGeo tile_geo(const DasArgs& a, int ix0, int iz0) {
     const Geom& g = a.g;
     TileGeo t;
@@ -222,20 +223,23 @@ __device__ __forceinline__ TileGeo tile_geo(const DasArgs& a, int ix0, int iz0) 
     t.cx = fma((double)ix0, a.gd.gdx, a.gd.gx0);
     t.cz = fma((double)iz0, a.gd.gdz, a.gd.gz0);
     t.xlo = pixel_x(g, ix0);
-    t.xhi = pixel_x(g, ix0 + kTX - 1);
+    t.xhi = pixel_x(g, ix0 + COLS - 1);
     t.zlo = pixel_z(g, iz0);
-    t.zhi = pixel_z(g, iz0 + 8 * P - 1);
+    t.zhi = pixel_z(g, iz0 + ROWS - 1);
     t.er = tile_elements(g, t.xlo, t.xhi, t.zhi);
     return t;
 }
 
 // Staging window of one (transmit, receive chunk) stage: the first staged
-// sample lo (multiple of 8), the staged length (multiple of 8), and the FP32
-// window-relative base B = tx_ref + R_{r0} - lo.
+// sample lo (multiple of 8), the staged length (multiple of 8, <= W), the FP32
+// window-relative base B = tx_ref + R_{r0} - lo, and flags (bit 0: no sample of
+// the window is inside the record; bits 1..: clamped over-long window length).
 struct StageInfo {
-    int lo, len, skip, over;   // over: the window was longer than the shared stride (clamped)
+    int lo, len;
     float B;
-    float pad2[3];
+    int flags;
+    __device__ __forceinline__ bool skip() const { return flags & 1; }
+    __device__ __forceinline__ int over() const { return flags >> 1; }
 };
 
 __device__ __forceinline__ StageInfo make_stage(const DasArgs& a, float mn, float mx, double txref,
@@ -243,11 +247,60 @@ __device__ __forceinline__ StageInfo make_stage(const DasArgs& a, float mn, floa
     StageInfo si;
     si.lo = ((int)floorf(mn) - 2) & ~7;
     si.len = (((int)ceilf(mx) + 2 - si.lo + 1) + 7) & ~7;
-    si.skip = (si.lo + si.len <= 0 || si.lo > a.ns - 2) ? 1 : 0;
+    const int skip = (si.lo + si.len <= 0 || si.lo > a.ns - 2) ? 1 : 0;
     si.B = (float)(txref + R_r0 - (double)si.lo);
-    si.over = si.len > a.W ? si.len : 0;
-    if (si.over) si.len = a.W;
+    const int over = si.len > a.W ? si.len : 0;
+    if (over) si.len = a.W;
+    si.flags = skip | (over << 1);
     return si;
+}
+
+// ---------------------------------------------------------------------------
+// TMA staging: bulk asynchronous copies (cp.async.bulk) of raw trace windows
+// into a shared-memory ring, completion tracked by mbarriers.  Every wait is
+// bounded: on timeout the kernel records a flag in the workspace header and
+// carries on (its result is then unspecified, the call reports WF_ERR_INTERNAL
+// through wf_workspace_check) instead of spinning forever.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0u;
+}
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes,
+                                              unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void fence_async_shared() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+constexpr unsigned kWaitLimit = 1u << 22;   // try_wait rounds before a wait is declared stuck
+
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity) {
+    for (unsigned i = 0; i < kWaitLimit; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (i >= 16) __nanosleep(64);
+    }
+    return false;
 }
 
 // Raw samples of one staging segment (8 consecutive samples + the next one)
@@ -256,24 +309,23 @@ template <typename T> struct Seg;
 template <> struct Seg<int16_t> {
     uint4 v;
     int nxt;
-    __device__ __forceinline__ float at(int k, float s) const {
-        const unsigned word = (k >> 1) == 0 ? v.x : (k >> 1) == 1 ? v.y : (k >> 1) == 2 ? v.z : v.w;
-        const int q = (k & 1) ? ((int)word >> 16) : (int)(short)(word & 0xffffu);
-        return (float)q * s;
+    __device__ __forceinline__ float at(int k) const {
+        const unsigned w = (k >> 1) == 0 ? v.x : (k >> 1) == 1 ? v.y : (k >> 1) == 2 ? v.z : v.w;
+        return (float)((k & 1) ? ((int)w >> 16) : (int)(short)(w & 0xffffu));
     }
 };
 template <> struct Seg<__half> {
     uint4 v;
     int nxt;
-    __device__ __forceinline__ float at(int k, float) const {
-        const unsigned word = (k >> 1) == 0 ? v.x : (k >> 1) == 1 ? v.y : (k >> 1) == 2 ? v.z : v.w;
-        return __half2float(__ushort_as_half((unsigned short)((k & 1) ? (word >> 16) : (word & 0xffffu))));
+    __device__ __forceinline__ float at(int k) const {
+        const unsigned w = (k >> 1) == 0 ? v.x : (k >> 1) == 1 ? v.y : (k >> 1) == 2 ? v.z : v.w;
+        return __half2float(__ushort_as_half((unsigned short)((k & 1) ? (w >> 16) : (w & 0xffffu))));
     }
 };
 template <> struct Seg<float> {
     float4 v0, v1;
     int nxt;
-    __device__ __forceinline__ float at(int k, float) const {
+    __device__ __forceinline__ float at(int k) const {
         switch (k) {
             case 0: return v0.x; case 1: return v0.y; case 2: return v0.z; case 3: return v0.w;
             case 4: return v1.x; case 5: return v1.y; case 6: return v1.z; default: return v1.w;
@@ -281,28 +333,25 @@ template <> struct Seg<float> {
     }
 };
 
-template <typename T> __device__ __forceinline__ float raw_one(int bits, float s);
-template <> __device__ __forceinline__ float raw_one<int16_t>(int bits, float s) { return (float)(short)bits * s; }
-template <> __device__ __forceinline__ float raw_one<__half>(int bits, float) {
+template <typename T> __device__ __forceinline__ float raw_one(int bits);
+template <> __device__ __forceinline__ float raw_one<int16_t>(int bits) { return (float)(short)bits; }
+template <> __device__ __forceinline__ float raw_one<__half>(int bits) {
     return __half2float(__ushort_as_half((unsigned short)bits));
 }
-template <> __device__ __forceinline__ float raw_one<float>(int bits, float) { return __int_as_float(bits); }
+template <> __device__ __forceinline__ float raw_one<float>(int bits) { return __int_as_float(bits); }
 
 template <typename T> __device__ __forceinline__ int raw_bits(const T* p);
-template <> __device__ __forceinline__ int raw_bits<int16_t>(const int16_t* p) { return (int)(unsigned short)__ldg(p); }
+template <> __device__ __forceinline__ int raw_bits<int16_t>(const int16_t* p) {
+    return (int)(unsigned short)__ldg(p);
+}
 template <> __device__ __forceinline__ int raw_bits<__half>(const __half* p) {
     return (int)__ldg(reinterpret_cast<const unsigned short*>(p));
 }
 template <> __device__ __forceinline__ int raw_bits<float>(const float* p) { return __float_as_int(__ldg(p)); }
 
-// Load the 8 samples [n0, n0 + 8) of a trace and sample n0 + 8 (zeros outside [0, ns)).
+// Load samples [n0, n0 + 8) of a trace and sample n0 + 8 (zero outside [0, ns)).
 template <typename T>
-__device__ __forceinline__ void seg_load(Seg<T>& sg, const T* tr, int n0, int ns, bool vec_ok, bool row_ok) {
-    if (!row_ok) {
-        sg = Seg<T>{};
-        sg.nxt = 0;
-        return;
-    }
+__device__ __forceinline__ void seg_load(Seg<T>& sg, const T* tr, int n0, int ns, bool vec_ok) {
     if (vec_ok && n0 >= 0 && n0 + 8 <= ns) {
         if constexpr (sizeof(T) == 2) {
             sg.v = __ldg(reinterpret_cast<const uint4*>(tr + n0));
@@ -329,16 +378,29 @@ __device__ __forceinline__ void seg_load(Seg<T>& sg, const T* tr, int n0, int ns
     sg.nxt = (n0 + 8 >= 0 && n0 + 8 < ns) ? raw_bits<T>(tr + n0 + 8) : 0;
 }
 
-// Convert a segment to 8 FP32 pairs (x[n], x[n+1] - x[n]); pairs whose n is
-// outside [0, ns - 2] are zero (no recorded neighbour).
+// Load samples [8k, 8k + 9) of a raw shared-memory row (16-byte aligned).
 template <typename T>
-__device__ __forceinline__ void seg_store(const Seg<T>& sg, float2* dst, int n0, int ns, float scale) {
+__device__ __forceinline__ void seg_load_smem(Seg<T>& sg, const T* row, int k) {
+    if constexpr (sizeof(T) == 2) {
+        sg.v = *reinterpret_cast<const uint4*>(row + 8 * k);
+        sg.nxt = (int)*reinterpret_cast<const unsigned short*>(row + 8 * k + 8);
+    } else {
+        sg.v0 = *reinterpret_cast<const float4*>(row + 8 * k);
+        sg.v1 = *reinterpret_cast<const float4*>(row + 8 * k + 4);
+        sg.nxt = __float_as_int(row[8 * k + 8]);
+    }
+}
+
+// Convert a segment to 8 FP32 pairs (x[n], x[n+1] - x[n]) in raw units; pairs
+// whose n is outside [0, ns - 2] are zero (no recorded neighbour).
+template <typename T>
+__device__ __forceinline__ void seg_store(const Seg<T>& sg, float2* dst, int n0, int ns) {
     float v[9];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) v[k] = sg.at(k, scale);
-    v[8] = raw_one<T>(sg.nxt, scale);
-    float4 o[4];
-    const bool full = n0 >= 0 && n0 + 8 <= ns - 1;
+    for (int k = 0; k < 8; ++k) v[k] = sg.at(k);
+    v[8] = raw_one<T>(sg.nxt);
+    const bool full = n0 >= 0 && n0 + 9 <= ns;
+    float4* d4 = reinterpret_cast<float4*>(dst);
 #pragma unroll
     for (int k = 0; k < 8; k += 2) {
         float2 p0 = make_float2(v[k], v[k + 1] - v[k]);
@@ -347,44 +409,43 @@ __device__ __forceinline__ void seg_store(const Seg<T>& sg, float2* dst, int n0,
             if (!(n0 + k >= 0 && n0 + k <= ns - 2)) p0 = make_float2(0.0f, 0.0f);
             if (!(n0 + k + 1 >= 0 && n0 + k + 1 <= ns - 2)) p1 = make_float2(0.0f, 0.0f);
         }
-        o[k >> 1] = make_float4(p0.x, p0.y, p1.x, p1.y);
+        d4[k >> 1] = make_float4(p0.x, p0.y, p1.x, p1.y);
     }
-    float4* d4 = reinterpret_cast<float4*>(dst);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) d4[k] = o[k];
 }
 
-template <typename T, int P>
+// Segment g = 64 c + k (c: trace of the chunk, k: 8-sample block) of a stage;
+// thread tid handles segments tid and tid + 256.
+template <typename T>
 __device__ __forceinline__ void stage_prefetch(Seg<T> (&sg)[2], const DasArgs& a, const T* rf,
                                                const StageInfo& si, int t, int r0, int r_last,
                                                bool vec_ok) {
     const int nseg = si.len >> 3;
-    const float inv = 1.0f / (float)nseg;
+    const int k = threadIdx.x & 63;
+    const T* base = rf + ((long long)t * a.g.n_elements + r0) * a.ns;
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
-        const int gidx = threadIdx.x + i * kThreads;
-        if (gidx < kC * nseg) {
-            const int c = (int)(((float)gidx + 0.5f) * inv);
-            const int k = gidx - c * nseg;
-            const int r = r0 + c;
-            const T* tr = rf + ((long long)t * a.g.n_elements + min(r, a.g.n_elements - 1)) * a.ns;
-            seg_load<T>(sg[i], tr, si.lo + 8 * k, a.ns, vec_ok, r <= r_last);
-        }
+        const int c = (threadIdx.x >> 6) + 4 * i;
+        if (k < nseg && r0 + c <= r_last) seg_load<T>(sg[i], base + (long long)c * a.ns, si.lo + 8 * k, a.ns, vec_ok);
     }
 }
 
 template <typename T>
 __device__ __forceinline__ void stage_store(const Seg<T> (&sg)[2], float2* buf, const DasArgs& a,
-                                            const StageInfo& si) {
+                                            const StageInfo& si, int r0, int r_last) {
     const int nseg = si.len >> 3;
-    const float inv = 1.0f / (float)nseg;
+    const int k = threadIdx.x & 63;
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
-        const int gidx = threadIdx.x + i * kThreads;
-        if (gidx < kC * nseg) {
-            const int c = (int)(((float)gidx + 0.5f) * inv);
-            const int k = gidx - c * nseg;
-            seg_store<T>(sg[i], buf + c * a.W + 8 * k, si.lo + 8 * k, a.ns, a.rf_scale);
+        const int c = (threadIdx.x >> 6) + 4 * i;
+        if (k < nseg) {
+            float2* dst = buf + c * a.W + 8 * k;
+            if (r0 + c <= r_last) {
+                seg_store<T>(sg[i], dst, si.lo + 8 * k, a.ns);
+            } else {
+                float4* d4 = reinterpret_cast<float4*>(dst);
+                const float4 z = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                d4[0] = z; d4[1] = z; d4[2] = z; d4[3] = z;
+            }
         }
     }
 }
@@ -400,53 +461,83 @@ __device__ __forceinline__ float warp_max(float v) {
     return v;
 }
 
-// Window of stage (slice transmit j, chunk starting at r0), computed by one
-// warp: lane c (mod 8) bounds receive element r0 + c, then min/max over lanes.
-template <int MODE>
-__device__ __forceinline__ StageInfo warp_stage_info(const DasArgs& a, const TileGeo& tg,
-                                                     const TxInfo& ti, double txref, int r0,
-                                                     int r_last, double R_r0) {
-    const int r = min(r0 + (threadIdx.x & 7), r_last);
-    const float2 bd = pair_bounds<MODE>(a.g, ti, r, tg.xlo, tg.xhi, tg.zlo, tg.zhi);
-    return make_stage(a, warp_min(bd.x), warp_max(bd.y), txref, R_r0);
+// Transmits per slice: STAI keeps a per-pixel transmit table in shared memory,
+// so wide-P tiles take fewer transmits per slice.
+template <int MODE, int P>
+struct Slice {
+    static constexpr int kTx = (MODE == 0 && P > 2) ? 8 : kTS;
+};
+constexpr int kTableStages = 256;  // stage-window ring in shared memory
+constexpr int kTableBatch = 128;   // windows computed per refill (one per thread)
+constexpr int kMaxRing = 3;        // TMA raw-sample ring depth
+
+// Shared-memory layout of the tiled kernel (byte offsets, all 16-byte aligned).
+struct SmemLayout {
+    size_t pairs, ttab, table, elems, raw, total;
+};
+
+__host__ __device__ inline SmemLayout smem_layout(int mode, int P, int ts, int W, int n_elements,
+                                                  bool db, bool tma, int ring, int rf_bytes) {
+    SmemLayout L;
+    size_t off = 0;
+    L.pairs = off;
+    off += (size_t)(db ? 2 : 1) * kC * W * sizeof(float2);
+    L.ttab = off;
+    off += mode == 0 ? (size_t)ts * P * kThreads * sizeof(float2) : 0;
+    L.table = off;
+    off += (size_t)kTableStages * sizeof(StageInfo);
+    L.elems = off;
+    off += (((size_t)n_elements * sizeof(Elem)) + 15) & ~(size_t)15;
+    L.raw = off;
+    off += tma ? (size_t)ring * kC * (W + 8) * rf_bytes : 0;
+    L.total = off;
+    return L;
 }
 
-template <int MODE, typename T, int P, bool CHECK>
+template <int MODE, typename T, int WCOL, int P, bool DB, bool TMA, bool CHECK>
 __global__ void __launch_bounds__(kThreads, 2) das_tiled_kernel(const __grid_constant__ DasArgs a) {
+    using S = Shape<WCOL, P>;
+    constexpr int TS = Slice<MODE, P>::kTx;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2* buf = reinterpret_cast<float2*>(smem_raw);                  // [kC][W] sample pairs
-    float2* ttab = buf + kC * a.W;                                       // [kTS][P][kThreads]
-    Elem* el = reinterpret_cast<Elem*>(ttab + kTS * P * kThreads);       // [E]
-    __shared__ double s_txref[kTS];
-    __shared__ float2 s_dtw[kTS][kThreads / 32];   // per-warp min/max transmit correction
-    __shared__ int s_tlist[kTS];
+    const SmemLayout L = smem_layout(MODE, P, TS, a.W, a.g.n_elements, DB, TMA, a.ring, (int)sizeof(T));
+    float2* buf0 = reinterpret_cast<float2*>(smem_raw + L.pairs);   // [DB+1][kC][W] pairs
+    float2* ttab = reinterpret_cast<float2*>(smem_raw + L.ttab);    // [TS][P][256] (STAI)
+    StageInfo* st = reinterpret_cast<StageInfo*>(smem_raw + L.table);
+    Elem* el = reinterpret_cast<Elem*>(smem_raw + L.elems);         // [E range]
+    T* raw = reinterpret_cast<T*>(smem_raw + L.raw);                // [ring][kC][W + 8]
+    __shared__ __align__(8) unsigned long long s_bar[kMaxRing];
+    __shared__ double s_txref[TS];
+    __shared__ float2 s_dtw[TS][kThreads / 32];   // STAI: per-warp range of the transmit correction
+    __shared__ int s_tlist[TS];
     __shared__ int s_nact;
-    __shared__ StageInfo s_si[2];
 
     const Geom& g = a.g;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int lx = lane & 3, lz = lane >> 2;
+    const int lx = lane % WCOL, lz = lane / WCOL;
     const int item = blockIdx.x, b = blockIdx.y;
     const int slice = item % a.n_slices, tile = item / a.n_slices;
-    const TileGeo tg = tile_geo<P>(a, (tile % a.tiles_x) * kTX, (tile / a.tiles_x) * (8 * P));
+    const TileGeo tg = tile_geo<S::kCols, S::kRows>(a, (tile % a.tiles_x) * S::kCols,
+                                                    (tile / a.tiles_x) * S::kRows);
     const T* rf = reinterpret_cast<const T*>(a.rf) + (long long)b * a.frame_elems;
     const bool vec_ok = (a.ns & 7) == 0;
+    const int RW = a.W + 8;           // raw row stride (samples)
+    const int ring = TMA ? a.ring : 1;
 
-    // Pixel offsets from the reference point: column 4 warp + lx, rows lz + 8 p.
-    const int col = 4 * warp + lx;
+    // Pixel offsets from the reference point: column WCOL warp + lx, rows lz + kLR p.
+    const int col = WCOL * warp + lx;
     const float ux = (float)col * g.gdx;
     float kz[P], kap[P], uz[P];
 #pragma unroll
     for (int p = 0; p < P; ++p) {
-        uz[p] = (float)(lz + 8 * p) * g.gdz;
+        uz[p] = (float)(lz + S::kLR * p) * g.gdz;
         kz[p] = uz[p] * fmaf(2.0f, (float)tg.cz, uz[p]);
         kap[p] = aperture_kappa(g, (float)tg.cz + uz[p]);
     }
-    // Elements that can weigh on this warp's 4 columns (all rows of the tile).
-    const int2 wr = tile_elements(g, pixel_x(g, tg.ix0 + 4 * warp), pixel_x(g, tg.ix0 + 4 * warp + 3),
-                                  tg.zhi);
+    // Elements that can weigh on this warp's columns (all rows of the tile).
+    const int2 wr = tile_elements(g, pixel_x(g, tg.ix0 + WCOL * warp),
+                                  pixel_x(g, tg.ix0 + WCOL * warp + WCOL - 1), tg.zhi);
 
-    const int t_begin = slice * kTS, t_end = min(a.n_tx, t_begin + kTS);
+    const int t_begin = slice * TS, t_end = min(a.n_tx, t_begin + TS);
     const int2 er = tg.er;
     for (int e = er.x + tid; e <= er.y; e += kThreads) el[e - er.x] = make_elem(a, tg.cx, tg.cz, e);
     if (tid == 0) {
@@ -456,38 +547,80 @@ __global__ void __launch_bounds__(kThreads, 2) das_tiled_kernel(const __grid_con
             s_tlist[n++] = t;
         }
         s_nact = er.x <= er.y ? n : 0;
+        if (TMA) {
+            for (int i = 0; i < ring; ++i) mbar_init(&s_bar[i], 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
     }
     __syncthreads();
     const int n_act = s_nact;
 
-    // Transmit terms of the slice: FP32 per-pixel correction + weight (thread-private table),
-    // FP64 reference per transmit, per-warp range of the corrections.
     for (int j = 0; j < n_act; ++j) {
         const TxInfo& ti = a.tx[s_tlist[j]];
-        float mn = 3.0e38f, mx = -3.0e38f;
+        if (MODE == 0) {
+            // STAI transmit terms: FP32 correction + weight per pixel, per-warp range.
+            const Elem et = el[ti.e - er.x];
+            float mn = 3.0e38f, mx = -3.0e38f;
 #pragma unroll
-        for (int p = 0; p < P; ++p) {
-            float2 v;
-            if (MODE == 0) {
-                const Elem et = el[ti.e - er.x];
-                v.x = dist_delta(et, ux, kz[p]);
-                v.y = apod_w(g.apod, -(et.ax + ux), kap[p]) * et.g;
-            } else {
-                v.x = fmaf(ux, ti.sin_f, uz[p] * ti.cos_f);
-                v.y = 1.0f;
+            for (int p = 0; p < P; ++p) {
+                const float2 v = make_float2(dist_delta(et, ux, kz[p]),
+                                             apod_w(g.apod, -(et.ax + ux), kap[p]) * et.g);
+                mn = fminf(mn, v.x);
+                mx = fmaxf(mx, v.x);
+                ttab[(j * P + p) * kThreads + tid] = v;
             }
-            mn = fminf(mn, v.x);
-            mx = fmaxf(mx, v.x);
-            ttab[(j * P + p) * kThreads + tid] = v;
+            mn = warp_min(mn);
+            mx = warp_max(mx);
+            if (lane == 0) s_dtw[j][warp] = make_float2(mn, mx);
         }
-        mn = warp_min(mn);
-        mx = warp_max(mx);
-        if (lane == 0) s_dtw[j][warp] = make_float2(mn, mx);
-        if (tid == j) s_txref[j] = tx_ref<MODE>(ti, tg.cx, tg.cz, MODE == 0 ? el[ti.e - er.x].R : 0.0);
+        if (tid == j) s_txref[j] = tx_ref<MODE>(ti, tg.cx, tg.cz, MODE == 0 ? elem_R(el[ti.e - er.x]) : 0.0);
     }
     const int n_chunks = n_act > 0 ? (er.y - er.x + kC) / kC : 0;
     const int n_stages = n_chunks * n_act;
     __syncthreads();
+
+    // Stage windows, kTableBatch at a time into a ring of kTableStages: stage q
+    // is (slice transmit q mod n_act, receive chunk q / n_act).
+    auto fill_table = [&](int base) {
+        const int q = base + tid;
+        if (tid < kTableBatch && q < n_stages) {
+            const int k = q / n_act, jj = q - k * n_act;
+            const int rr0 = er.x + k * kC, rrl = min(rr0 + kC - 1, er.y);
+            const TxInfo& ti = a.tx[s_tlist[jj]];
+            float mn = 3.0e38f, mx = -3.0e38f;
+            for (int rr = rr0; rr <= rrl; ++rr) {
+                const float2 bd = pair_bounds<MODE>(g, ti, rr, tg.xlo, tg.xhi, tg.zlo, tg.zhi);
+                mn = fminf(mn, bd.x);
+                mx = fmaxf(mx, bd.y);
+            }
+            st[q & (kTableStages - 1)] = make_stage(a, mn, mx, s_txref[jj], elem_R(el[rr0 - er.x]));
+        }
+    };
+    // TMA producer (thread 0): raw windows of stage qq into ring slot qq % ring.
+    auto issue = [&](int qq) {
+        const StageInfo si = st[qq & (kTableStages - 1)];
+        unsigned long long* bar = &s_bar[qq % ring];
+        const int k = qq / n_act, jj = qq - k * n_act;
+        const int rr0 = er.x + k * kC, rrl = min(rr0 + kC - 1, er.y);
+        const int na = max(si.lo, 0), nb = min(si.lo + si.len + 8, a.ns);
+        if (si.skip() || nb <= na) {
+            mbar_arrive_expect(bar, 0u);
+            return;
+        }
+        const unsigned bytes = (unsigned)((nb - na) * (int)sizeof(T));
+        fence_async_shared();
+        mbar_arrive_expect(bar, bytes * (unsigned)(rrl - rr0 + 1));
+        T* slot = raw + (size_t)(qq % ring) * kC * RW;
+        const T* src = rf + ((long long)s_tlist[jj] * g.n_elements + rr0) * a.ns + na;
+        for (int c = 0; c <= rrl - rr0; ++c)
+            bulk_copy_g2s(slot + c * RW + (na - si.lo), src + (long long)c * a.ns, bytes, bar);
+    };
+    const int ahead = TMA ? ring - 1 : 1;   // stages in flight ahead of the one being converted
+    fill_table(0);
+
+    // PWI: range of the transmit correction ux sin + uz cos over this warp's pixels.
+    const float wux0 = (float)(WCOL * warp) * g.gdx, wux1 = (float)(WCOL * warp + WCOL - 1) * g.gdx;
+    const float wuz1 = (float)(S::kRows - 1) * g.gdz;
 
     float acc[P];
 #pragma unroll
@@ -497,99 +630,133 @@ __global__ void __launch_bounds__(kThreads, 2) das_tiled_kernel(const __grid_con
     unsigned cmask = 0u;
     Seg<T> sg[2];
 
-    // Stage infos are computed by warp 0 two stages ahead (double-buffered in
-    // shared memory); every thread prefetches its raw samples one stage ahead.
-    auto stage_of = [&](int qq, int& jj, int& rr0, int& rrl) {
-        const int kk = qq / n_act;
-        jj = qq - kk * n_act;
-        rr0 = er.x + kk * kC;
-        rrl = min(rr0 + kC - 1, er.y);
+    int j = 0, r0 = er.x;           // stage q = (chunk starting at r0, slice transmit j)
+    int j1 = 0, r01 = er.x;         // stage q + 1 (register path)
+    auto advance = [&](int& jj, int& rr) {
+        if (++jj == n_act) { jj = 0; rr += kC; }
     };
-    auto info_for = [&](int qq) {
-        int jj, rr0, rrl;
-        stage_of(qq, jj, rr0, rrl);
-        return warp_stage_info<MODE>(a, tg, a.tx[s_tlist[jj]], s_txref[jj], rr0, rrl,
-                                     el[rr0 - er.x].R);
-    };
+    __syncthreads();
     if (n_stages > 0) {
-        if (warp == 0) {
-            const StageInfo s0 = info_for(0);
-            if (lane == 0) s_si[0] = s0;
-        }
-        __syncthreads();
-        const StageInfo s0 = s_si[0];
-        if (!s0.skip) stage_prefetch<T, P>(sg, a, rf, s0, s_tlist[0], er.x, min(er.x + kC - 1, er.y), vec_ok);
-        if (warp == 0 && n_stages > 1) {
-            const StageInfo s1 = info_for(1);
-            if (lane == 0) s_si[1] = s1;
+        advance(j1, r01);
+        if (TMA) {
+            if (tid == 0)
+                for (int qq = 0; qq < min(ahead, n_stages); ++qq) issue(qq);
+        } else {
+            const StageInfo s0 = st[0];
+            if (!s0.skip()) stage_prefetch<T>(sg, a, rf, s0, s_tlist[0], er.x, min(er.x + kC - 1, er.y), vec_ok);
         }
     }
 
     for (int q = 0; q < n_stages; ++q) {
-        int j, r0, r_last;
-        stage_of(q, j, r0, r_last);
-        const StageInfo si = s_si[q & 1];
+        const int r_last = min(r0 + kC - 1, er.y);
+        const StageInfo si = st[q & (kTableStages - 1)];
         const int t = s_tlist[j];
-        if (si.over && tid == 0) flag(a.hdr, 1u, (unsigned)blockIdx.x, (unsigned)si.over, (unsigned)a.W);
-        if (!si.skip) stage_store<T>(sg, buf, a, si);
-        __syncthreads();   // pairs of stage q visible; info of stage q + 1 visible
-        if (q + 1 < n_stages) {
-            int j1, r01, rl1;
-            stage_of(q + 1, j1, r01, rl1);
-            const StageInfo s1 = s_si[(q + 1) & 1];
-            if (!s1.skip) stage_prefetch<T, P>(sg, a, rf, s1, s_tlist[j1], r01, rl1, vec_ok);
-        }
-        if (warp == 0 && q + 2 < n_stages) {
-            const StageInfo s2 = info_for(q + 2);
-            if (lane == 0) s_si[q & 1] = s2;
-        }
-        if (j == 0) {
-            // Receive chunk: window-relative distances C_c + delta and weights in registers;
-            // the warp's active elements and range of the receive term.
-            const double R0 = el[r0 - er.x].R;
-            cmask = 0u;
-            float mn = 3.0e38f, mx = -3.0e38f;
+        float2* buf = buf0 + (DB ? (q & 1) * kC * a.W : 0);
+        if (si.over() && tid == 0) flag(a.hdr, 1u, (unsigned)blockIdx.x, (unsigned)si.over(), (unsigned)a.W);
+        if (TMA) {
+            if (!mbar_wait_bounded(&s_bar[q % ring], (unsigned)((q / ring) & 1))) {
+                if (tid == 0) flag(a.hdr, 4u, (unsigned)blockIdx.x, (unsigned)q, 0u);
+            }
+            if (!si.skip()) {
+                // raw slot -> FP32 pairs, segment (trace c, block k) = (tid >> 6 [+4], tid & 63)
+                const T* slot = raw + (size_t)(q % ring) * kC * RW;
+                const int nseg = si.len >> 3, k = tid & 63;
 #pragma unroll
-            for (int c = 0; c < kC; ++c) {
-                const int re = min(r0 + c, r_last);  // padding reuses the last element, weight 0
-                const Elem ee = el[re - er.x];
-                const float cc = (float)(ee.R - R0);
-                const bool on = r0 + c <= r_last && r0 + c >= wr.x && r0 + c <= wr.y;
-                if (on) cmask |= 1u << c;
-#pragma unroll
-                for (int p = 0; p < P; ++p) {
-                    Dr[c][p] = cc + dist_delta(ee, ux, kz[p]);
-                    Wr[c][p] = on ? apod_w(g.apod, -(ee.ax + ux), kap[p]) * ee.g : 0.0f;
-                    if (on) {
-                        mn = fminf(mn, Dr[c][p]);
-                        mx = fmaxf(mx, Dr[c][p]);
+                for (int i = 0; i < 2; ++i) {
+                    const int c = (tid >> 6) + 4 * i;
+                    if (k < nseg) {
+                        float2* dst = buf + c * a.W + 8 * k;
+                        if (r0 + c <= r_last) {
+                            Seg<T> sv;
+                            seg_load_smem<T>(sv, slot + c * RW, k);
+                            seg_store<T>(sv, dst, si.lo + 8 * k, a.ns);
+                        } else {
+                            float4* d4 = reinterpret_cast<float4*>(dst);
+                            const float4 z = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                            d4[0] = z; d4[1] = z; d4[2] = z; d4[3] = z;
+                        }
                     }
                 }
             }
-            dr_min = warp_min(mn);
-            dr_max = warp_max(mx);
+        } else if (!si.skip()) {
+            stage_store<T>(sg, buf, a, si, r0, r_last);
+        }
+        __syncthreads();   // pairs of stage q visible; raw slot of stage q - 1 and (double-buffered) pairs of q - 1 free
+        if (q + ahead < n_stages) {
+            if (((q + ahead) & (kTableBatch - 1)) == 0) {
+                fill_table(q + ahead);
+                __syncthreads();
+            }
+            if (TMA) {
+                if (tid == 0) issue(q + ahead);
+            } else {
+                const StageInfo s1 = st[(q + 1) & (kTableStages - 1)];
+                if (!s1.skip()) stage_prefetch<T>(sg, a, rf, s1, s_tlist[j1], r01, min(r01 + kC - 1, er.y), vec_ok);
+            }
+        }
+        if (j == 0) {
+            // New receive chunk: which elements weigh on this warp, and (only for those)
+            // window-relative distances C_c + delta and weights (times the int16 scale).
+            cmask = 0u;
+#pragma unroll
+            for (int c = 0; c < kC; ++c)
+                if (r0 + c <= r_last && r0 + c >= wr.x && r0 + c <= wr.y) cmask |= 1u << c;
+            if (cmask) {
+                const Elem e0 = el[r0 - er.x];
+                float mn = 3.0e38f, mx = -3.0e38f;
+#pragma unroll
+                for (int c = 0; c < kC; ++c) {
+                    const bool on = (cmask >> c) & 1u;
+                    const Elem ee = el[(on ? r0 + c : r0) - er.x];
+                    const float cc = elem_rel(ee, e0);
+#pragma unroll
+                    for (int p = 0; p < P; ++p) {
+                        Dr[c][p] = on ? cc + dist_delta(ee, ux, kz[p]) : 0.0f;
+                        Wr[c][p] = on ? apod_w(g.apod, -(ee.ax + ux), kap[p]) * (ee.g * a.rf_scale) : 0.0f;
+                        if (on) {
+                            mn = fminf(mn, Dr[c][p]);
+                            mx = fmaxf(mx, Dr[c][p]);
+                        }
+                    }
+                }
+                dr_min = warp_min(mn);
+                dr_max = warp_max(mx);
+            }
         }
         // Warp-level skip: transmit or chunk outside this warp's aperture, or every
         // delay of the warp outside the record.
-        bool live = !si.skip && cmask != 0u;
-        if (MODE == 0) live = live && a.tx[t].e >= wr.x && a.tx[t].e <= wr.y;
+        bool live = !si.skip() && cmask != 0u;
+        float2 dtw;
+        if (MODE == 0) {
+            live = live && a.tx[t].e >= wr.x && a.tx[t].e <= wr.y;
+            dtw = s_dtw[j][warp];
+        } else {
+            const float sn = a.tx[t].sin_f, cs = a.tx[t].cos_f;
+            const float v0 = wux0 * sn, v1 = wux1 * sn, z1 = wuz1 * cs;
+            dtw = make_float2(fminf(v0, v1) + fminf(0.0f, z1), fmaxf(v0, v1) + fmaxf(0.0f, z1));
+        }
         if (live) {
-            const float2 dtw = s_dtw[j][warp];
             const float lo_f = (float)si.lo + si.B;
             live = (lo_f + dtw.x + dr_min <= (float)(a.ns - 1) + 0.5f) && (lo_f + dtw.y + dr_max >= -0.5f);
         }
         if (live) {
             float tw[P], wt[P], acct[P];
+            const float sn = a.tx[t].sin_f, cs = a.tx[t].cos_f;
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                const float2 v = ttab[(j * P + p) * kThreads + tid];
-                tw[p] = si.B + v.x;
-                wt[p] = v.y;
+                if (MODE == 0) {
+                    const float2 v = ttab[(j * P + p) * kThreads + tid];
+                    tw[p] = si.B + v.x;
+                    wt[p] = v.y;
+                } else {
+                    tw[p] = si.B + fmaf(ux, sn, uz[p] * cs);
+                    wt[p] = 1.0f;
+                }
                 acct[p] = 0.0f;
             }
 #pragma unroll
             for (int c = 0; c < kC; ++c) {
-                if (!(cmask & (1u << c))) continue;
+                if (!((cmask >> c) & 1u)) continue;
                 const float2* bc = buf + c * a.W;
 #pragma unroll
                 for (int p = 0; p < P; ++p) {
@@ -597,7 +764,7 @@ __global__ void __launch_bounds__(kThreads, 2) das_tiled_kernel(const __grid_con
                     const float m = __fadd_rd(s, kMagic);
                     const float f = s - (m - kMagic);
                     int idx = __float_as_int(m) - kMagicBits;
-                    if (CHECK && (idx < 0 || idx >= si.len || idx >= a.W)) {
+                    if (CHECK && (idx < 0 || idx >= si.len)) {
                         flag(a.hdr, 2u, (unsigned)blockIdx.x, (unsigned)idx, (unsigned)si.len);
                         idx = 0;
                     }
@@ -606,9 +773,11 @@ __global__ void __launch_bounds__(kThreads, 2) das_tiled_kernel(const __grid_con
                 }
             }
 #pragma unroll
-            for (int p = 0; p < P; ++p) acc[p] = fmaf(wt[p], acct[p], acc[p]);
+            for (int p = 0; p < P; ++p) acc[p] = MODE == 0 ? fmaf(wt[p], acct[p], acc[p]) : acc[p] + acct[p];
         }
-        __syncthreads();   // compute of stage q done before stage q + 1 overwrites the pairs
+        if (!DB) __syncthreads();   // single buffer: compute of stage q done before stage q + 1 lands
+        j = j1; r0 = r01;
+        advance(j1, r01);
     }
 
     // Partial tile in thread order: [p][tid].
@@ -618,17 +787,18 @@ __global__ void __launch_bounds__(kThreads, 2) das_tiled_kernel(const __grid_con
 }
 
 // Sum the transmit-slice partials of every pixel in slice order.
-template <int P>
+template <int WCOL, int P>
 __global__ void das_reduce_kernel(const float* __restrict__ part, float* __restrict__ out, int nz,
                                   int nx, int tiles_x, int n_slices, int n_items) {
+    using S = Shape<WCOL, P>;
     const int ix = blockIdx.x * blockDim.x + threadIdx.x;
     const int iz = blockIdx.y;
     const int b = blockIdx.z;
     if (ix >= nx) return;
-    const int tile = (iz / (8 * P)) * tiles_x + ix / kTX;
-    const int cl = ix % kTX, rl = iz % (8 * P);
-    const int tid = (cl >> 2) * 32 + (rl & 7) * 4 + (cl & 3);
-    const int local = (rl >> 3) * kThreads + tid;
+    const int tile = (iz / S::kRows) * tiles_x + ix / S::kCols;
+    const int cl = ix % S::kCols, rl = iz % S::kRows;
+    const int tid = (cl / WCOL) * 32 + (rl % S::kLR) * WCOL + (cl % WCOL);
+    const int local = (rl / S::kLR) * kThreads + tid;
     const float* p = part + ((long long)b * n_items + (long long)tile * n_slices) * (kThreads * P) + local;
     float s = 0.0f;
     for (int k = 0; k < n_slices; ++k) s += p[(long long)k * (kThreads * P)];
@@ -674,23 +844,23 @@ __global__ void __launch_bounds__(256) das_direct_kernel(const __grid_constant__
             const double s = dt + sqrt((pxd - xe) * (pxd - xe) + pzd * pzd);
             const double fl = floor(s);
             if (!(fl >= 0.0) || !(fl <= (double)(a.ns - 2))) continue;
-            const int i = (int)fl;
-            const float f = (float)(s - fl);
-            const float2 ab = RF<T>::pair(rf + ((long long)t * g.n_elements + r) * a.ns + i, a.rf_scale);
-            inner = fmaf(w, fmaf(f, ab.y, ab.x), inner);
+            const T* tr = rf + ((long long)t * g.n_elements + r) * a.ns + (int)fl;
+            const float x0 = raw_one<T>(raw_bits<T>(tr)), x1 = raw_one<T>(raw_bits<T>(tr + 1));
+            inner = fmaf(w, fmaf((float)(s - fl), x1 - x0, x0), inner);
         }
         acc = fmaf(wt, inner, acc);
     }
-    a.out[((long long)b * g.nz + iz) * g.nx + ix] = acc;
+    a.out[((long long)b * g.nz + iz) * g.nx + ix] = acc * a.rf_scale;
 }
 
 // Delays (samples) exactly as the tiled kernel forms them: the window start lo
 // plus the FP32 window-relative value, for (pixel, transmit, element) triples.
 // Triples the kernel never evaluates (element outside the tile's aperture
 // range, inactive transmit) are NaN.
-template <int MODE, int P>
+template <int MODE, int WCOL, int P>
 __global__ void das_delays_kernel(const __grid_constant__ DasArgs a, const int32_t* __restrict__ pix,
                                   int n_pix, double* __restrict__ out) {
+    using S = Shape<WCOL, P>;
     const Geom& g = a.g;
     const long long n = (long long)n_pix * a.n_tx * g.n_elements;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -700,7 +870,8 @@ __global__ void das_delays_kernel(const __grid_constant__ DasArgs a, const int32
         const int q = (int)(i / ((long long)g.n_elements * a.n_tx));
         const int lin = pix[q];
         const int ix = lin % g.nx, iz = lin / g.nx;
-        const TileGeo tg = tile_geo<P>(a, (ix / kTX) * kTX, (iz / (8 * P)) * (8 * P));
+        const TileGeo tg = tile_geo<S::kCols, S::kRows>(a, (ix / S::kCols) * S::kCols,
+                                                        (iz / S::kRows) * S::kRows);
         const TxInfo& ti = a.tx[t];
         const int2 er = tg.er;
         if (r < er.x || r > er.y || (MODE == 0 && (ti.e < er.x || ti.e > er.y))) {
@@ -718,7 +889,7 @@ __global__ void das_delays_kernel(const __grid_constant__ DasArgs a, const int32
         float dtx;
         if (MODE == 0) {
             const Elem et = make_elem(a, tg.cx, tg.cz, ti.e);
-            R_et = et.R;
+            R_et = elem_R(et);
             dtx = dist_delta(et, ux, kz);
         } else {
             dtx = fmaf(ux, ti.sin_f, uz * ti.cos_f);
@@ -729,8 +900,8 @@ __global__ void das_delays_kernel(const __grid_constant__ DasArgs a, const int32
             mn = fminf(mn, bd.x);
             mx = fmaxf(mx, bd.y);
         }
-        const StageInfo si = make_stage(a, mn, mx, tx_ref<MODE>(ti, tg.cx, tg.cz, R_et), e0.R);
-        const float dr = (float)(erl.R - e0.R) + dist_delta(erl, ux, kz);
+        const StageInfo si = make_stage(a, mn, mx, tx_ref<MODE>(ti, tg.cx, tg.cz, R_et), elem_R(e0));
+        const float dr = elem_rel(erl, e0) + dist_delta(erl, ux, kz);
         const float s = (si.B + dtx) + dr;
         out[i] = (double)si.lo + (double)s;
     }
@@ -790,66 +961,138 @@ double max_delay(const wf_probe* p, const wf_grid* g) {
     return std::sqrt(dx * dx + dz * dz) * sc;
 }
 
+// Kernel configurations in order of preference: columns per warp and pixels per lane.
+struct Cfg {
+    int wcol, p;
+};
+constexpr Cfg kStaiCfgs[] = {{4, 4}, {4, 2}};
+constexpr Cfg kPwiCfgs[] = {{4, 4}, {4, 2}};
+constexpr size_t kSmemBudget = 113 * 1024;   // two CTAs per SM
+constexpr size_t kMaxTiledSmem = 220 * 1024;  // one CTA per SM
+
 struct Plan {
+    Cfg cfg;
+    int cols, rows, ts;
     int tiles_x, tiles_z, n_slices, n_items;
-    int W, P;
-    bool tiled;
+    int W, ring;
+    bool tiled, db, tma;
     size_t smem;
     size_t ws_bytes;
 };
 
-// Upper bound on one staging window for a tile of kTX x 8P pixels: both
-// distance terms move by at most the tile diagonal, the receive term by
-// (kC - 1) pitches across the chunk; plus floor/ceil, the +-2 margins and the
+// Upper bound on one staging window for a cols x rows tile: both distance
+// terms move by at most the tile diagonal, the receive term by (kC - 1)
+// pitches across the chunk; plus floor/ceil, the +-2 margins and the
 // 8-sample alignment of both ends.
-int window_bound(const GeomD& D, int P) {
-    const double ex = (double)(kTX - 1) * D.gdx, ez = (double)(8 * P - 1) * D.gdz;
+int window_bound(const GeomD& D, int cols, int rows) {
+    const double ex = (double)(cols - 1) * D.gdx, ez = (double)(rows - 1) * D.gdz;
     const double diam = std::sqrt(ex * ex + ez * ez);
     const double w = 2.0 * diam + (kC - 1) * D.pitch + 24.0;
     return (int)std::ceil(w / 8.0) * 8;
 }
 
-Plan make_plan(const wf_probe* p, const wf_grid* g, int batch, int n_tx) {
-    Geom G;
-    GeomD D;
-    make_geom(p, g, G, D);
-    Plan P;
-    P.P = window_bound(D, 4) <= kMaxWindow ? 4 : 2;
-    P.W = window_bound(D, P.P);
+// Optional tuning override "wcol,p" (WF_DAS_TILE); ignored unless it names a
+// configuration of this mode that fits.
+bool tile_override(int mode, Cfg& out) {
+    const char* v = std::getenv("WF_DAS_TILE");
+    int w = 0, p = 0;
+    if (!v || std::sscanf(v, "%d,%d", &w, &p) != 2) return false;
+    const Cfg* cfgs = mode == 0 ? kStaiCfgs : kPwiCfgs;
+    for (int i = 0; i < 2; ++i)
+        if (cfgs[i].wcol == w && cfgs[i].p == p) {
+            out = cfgs[i];
+            return true;
+        }
+    return false;
+}
+
+Plan plan_for(int mode, const Cfg& cfg, const GeomD& D, const wf_probe* p, const wf_grid* g,
+              int batch, int n_tx, int ns, int rf_bytes) {
+    Plan P{};
+    P.cfg = cfg;
+    P.cols = 8 * cfg.wcol;
+    P.rows = (32 / cfg.wcol) * cfg.p;
+    P.ts = (mode == 0 && cfg.p > 2) ? 8 : kTS;
+    P.W = window_bound(D, P.cols, P.rows);
     P.tiled = P.W <= kMaxWindow;
-    P.tiles_x = (g->nx + kTX - 1) / kTX;
-    P.tiles_z = (g->nz + 8 * P.P - 1) / (8 * P.P);
-    P.n_slices = (n_tx + kTS - 1) / kTS;
+    P.tiles_x = (g->nx + P.cols - 1) / P.cols;
+    P.tiles_z = (g->nz + P.rows - 1) / P.rows;
+    P.n_slices = (n_tx + P.ts - 1) / P.ts;
     P.n_items = P.tiles_x * P.tiles_z * P.n_slices;
-    P.smem = (size_t)kC * P.W * sizeof(float2) + (size_t)kTS * P.P * kThreads * sizeof(float2) +
-             (size_t)p->n_elements * sizeof(Elem);
+    // TMA bulk copies need 16-byte aligned trace windows: samples per trace a multiple of 8.
+    // WF_DAS_NO_TMA=1 selects the register-staged path instead (tuning and testing).
+    const char* no_tma = std::getenv("WF_DAS_NO_TMA");
+    P.tma = ns % 8 == 0 && !(no_tma && no_tma[0] && no_tma[0] != '0');
+    bool found = false;
+    const int rings[2] = {P.tma ? 3 : 1, P.tma ? 2 : 1};
+    for (int ri = 0; ri < 2 && !found; ++ri)
+        for (int dbi = 0; dbi < 2 && !found; ++dbi) {
+            const bool db = dbi == 0 && P.tma;
+            const SmemLayout L = smem_layout(mode, cfg.p, P.ts, P.W, p->n_elements, db, P.tma, rings[ri], rf_bytes);
+            if (L.total <= kSmemBudget) {
+                P.ring = rings[ri];
+                P.db = db;
+                P.smem = L.total;
+                found = true;
+            }
+        }
+    if (!found) {
+        P.ring = P.tma ? 2 : 1;
+        P.db = false;
+        P.smem = smem_layout(mode, cfg.p, P.ts, P.W, p->n_elements, false, P.tma, P.ring, rf_bytes).total;
+        if (P.smem > kMaxTiledSmem) P.tiled = false;
+    }
     P.ws_bytes = kWsHeaderBytes +
-                 (P.tiled ? (size_t)batch * P.n_items * kThreads * P.P * sizeof(float) : 0);
+                 (P.tiled ? (size_t)batch * P.n_items * kThreads * cfg.p * sizeof(float) : 0);
     return P;
 }
 
-constexpr size_t kMaxTiledSmem = (size_t)kC * kMaxWindow * sizeof(float2) +
-                                  (size_t)kTS * 4 * kThreads * sizeof(float2) +
-                                  (size_t)WF_MAX_ELEMENTS * sizeof(Elem);
+Plan make_plan(int mode, const wf_probe* p, const wf_grid* g, int batch, int n_tx, int ns = 8,
+               int rf_bytes = 4) {
+    Geom G;
+    GeomD D;
+    make_geom(p, g, G, D);
+    Cfg forced;
+    if (tile_override(mode, forced)) {
+        const Plan P = plan_for(mode, forced, D, p, g, batch, n_tx, ns, rf_bytes);
+        if (P.tiled) return P;
+    }
+    const Cfg* cfgs = mode == 0 ? kStaiCfgs : kPwiCfgs;
+    const int n = mode == 0 ? 2 : 2;
+    Plan P{};
+    for (int i = 0; i < n; ++i) {
+        P = plan_for(mode, cfgs[i], D, p, g, batch, n_tx, ns, rf_bytes);
+        if (P.tiled) return P;
+    }
+    return P;
+}
 
 bool check_bounds_mode() {
     const char* v = std::getenv("WF_CHECK_BOUNDS");
     return v && v[0] && v[0] != '0';
 }
 
-template <int MODE, typename T, int P>
-wf_status launch_tiled(DasArgs& A, const Plan& PL, int batch, cudaStream_t st) {
+template <int MODE, typename T, int WCOL, int P, bool DB, bool TMA>
+wf_status launch_tiled_v(DasArgs& A, const Plan& PL, int batch, cudaStream_t st) {
     static unsigned long long smem_set[2] = {0ull, 0ull};
     const bool chk = check_bounds_mode();
-    auto kern = chk ? das_tiled_kernel<MODE, T, P, true> : das_tiled_kernel<MODE, T, P, false>;
+    auto kern = chk ? das_tiled_kernel<MODE, T, WCOL, P, DB, TMA, true>
+                    : das_tiled_kernel<MODE, T, WCOL, P, DB, TMA, false>;
     wf_status s = ensure_smem_limit(kern, kMaxTiledSmem, smem_set[chk ? 1 : 0]);
     if (s != WF_OK) return s;
     kern<<<dim3(PL.n_items, batch), kThreads, PL.smem, st>>>(A);
     if ((s = last_launch_status()) != WF_OK) return s;
     dim3 rg((A.g.nx + 127) / 128, A.g.nz, batch);
-    das_reduce_kernel<P><<<rg, 128, 0, st>>>(A.part, A.out, A.g.nz, A.g.nx, PL.tiles_x, PL.n_slices,
-                                             PL.n_items);
+    das_reduce_kernel<WCOL, P><<<rg, 128, 0, st>>>(A.part, A.out, A.g.nz, A.g.nx, PL.tiles_x,
+                                                   PL.n_slices, PL.n_items);
     return last_launch_status();
+}
+
+template <int MODE, typename T, int WCOL, int P>
+wf_status launch_tiled(DasArgs& A, const Plan& PL, int batch, cudaStream_t st) {
+    if (!PL.tma) return launch_tiled_v<MODE, T, WCOL, P, false, false>(A, PL, batch, st);
+    return PL.db ? launch_tiled_v<MODE, T, WCOL, P, true, true>(A, PL, batch, st)
+                 : launch_tiled_v<MODE, T, WCOL, P, false, true>(A, PL, batch, st);
 }
 
 template <int MODE, typename T>
@@ -859,7 +1102,8 @@ wf_status launch_das(DasArgs& A, const Plan& P, int batch, cudaStream_t st) {
         das_direct_kernel<MODE, T><<<grid, 256, 0, st>>>(A);
         return last_launch_status();
     }
-    return P.P == 4 ? launch_tiled<MODE, T, 4>(A, P, batch, st) : launch_tiled<MODE, T, 2>(A, P, batch, st);
+    return P.cfg.p == 4 ? launch_tiled<MODE, T, 4, 4>(A, P, batch, st)
+                        : launch_tiled<MODE, T, 4, 2>(A, P, batch, st);
 }
 
 template <int MODE>
@@ -887,7 +1131,7 @@ wf_status das_common(int mode, const wf_probe* probe, const wf_grid* grid, int32
     if (!rf || !out) return WF_ERR_INVALID_ARG;
     if (((uintptr_t)rf & 15u) || ((uintptr_t)out & 3u)) return WF_ERR_INVALID_ARG;
     if (2.0 * max_delay(probe, grid) + tx_extra >= 4194304.0) return WF_ERR_UNSUPPORTED;
-    const Plan P = make_plan(probe, grid, batch, n_tx);
+    const Plan P = make_plan(mode, probe, grid, batch, n_tx, n_samples, dtype == WF_F32 ? 4 : 2);
     if (!ws || ((uintptr_t)ws & 15u)) return WF_ERR_WORKSPACE;
     if (ws_bytes < P.ws_bytes) return WF_ERR_WORKSPACE;
     make_geom(probe, grid, A.g, A.gd);
@@ -897,7 +1141,7 @@ wf_status das_common(int mode, const wf_probe* probe, const wf_grid* grid, int32
     A.n_slices = P.n_slices;
     A.n_items = P.n_items;
     A.W = P.W;
-    A.P = P.P;
+    A.ring = P.ring;
     A.rf = rf;
     A.rf_scale = dtype == WF_I16 ? rf_scale : 1.0f;
     A.frame_elems = (long long)n_tx * probe->n_elements * n_samples;
@@ -924,7 +1168,8 @@ double fill_tx(DasArgs& a, const wf_probe* probe, int mode, int n_tx, const int3
             ti.e = e;
         } else {
             const double th = angles[t];
-            if (!std::isfinite(th)) return -1.0;
+            // steering beyond +-89 degrees has no plane wave travelling into the medium
+            if (!std::isfinite(th) || std::fabs(th) > 1.5533430342749532) return -1.0;
             ti.sin_d = std::sin(th);
             ti.cos_d = std::cos(th);
             ti.sin_f = (float)ti.sin_d;
@@ -944,7 +1189,14 @@ using namespace wf;
 extern "C" size_t wf_das_workspace_bytes(const wf_probe* probe, const wf_grid* grid, int32_t batch,
                                          int32_t n_tx) {
     if (check_probe_grid(probe, grid) != WF_OK || batch < 1 || n_tx < 1 || n_tx > WF_MAX_TX) return 0;
-    return make_plan(probe, grid, batch, n_tx).ws_bytes;
+    // Enough for every configuration either transmit scheme may pick.
+    Geom G;
+    GeomD D;
+    make_geom(probe, grid, G, D);
+    size_t need = kWsHeaderBytes;
+    for (const Cfg& c : kStaiCfgs) need = std::max(need, plan_for(0, c, D, probe, grid, batch, n_tx, 8, 4).ws_bytes);
+    for (const Cfg& c : kPwiCfgs) need = std::max(need, plan_for(1, c, D, probe, grid, batch, n_tx, 8, 4).ws_bytes);
+    return need;
 }
 
 extern "C" wf_status wf_das_stai(const wf_probe* probe, const wf_grid* grid, int32_t batch,
@@ -997,16 +1249,15 @@ extern "C" wf_status wf_das_delays(const wf_probe* probe, const wf_grid* grid, i
     make_geom(probe, grid, a.g, a.gd);
     a.n_tx = n_tx;
     a.ns = 1 << 30;  // the probe reports delays regardless of the record length
-    const Plan P = make_plan(probe, grid, 1, n_tx);
-    a.W = P.W;
-    a.P = P.P;
+    const Plan P = make_plan(mode, probe, grid, 1, n_tx);
+    a.W = 1 << 30;   // and never clamps a window
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (mode == 0) {
-        if (P.P == 4) das_delays_kernel<0, 4><<<304, 256, 0, st>>>(a, pix, n_pix, out);
-        else das_delays_kernel<0, 2><<<304, 256, 0, st>>>(a, pix, n_pix, out);
+        if (P.cfg.p == 4) das_delays_kernel<0, 4, 4><<<304, 256, 0, st>>>(a, pix, n_pix, out);
+        else das_delays_kernel<0, 4, 2><<<304, 256, 0, st>>>(a, pix, n_pix, out);
     } else {
-        if (P.P == 4) das_delays_kernel<1, 4><<<304, 256, 0, st>>>(a, pix, n_pix, out);
-        else das_delays_kernel<1, 2><<<304, 256, 0, st>>>(a, pix, n_pix, out);
+        if (P.cfg.p == 4) das_delays_kernel<1, 4, 4><<<304, 256, 0, st>>>(a, pix, n_pix, out);
+        else das_delays_kernel<1, 4, 2><<<304, 256, 0, st>>>(a, pix, n_pix, out);
     }
     return last_launch_status();
 }
