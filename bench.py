@@ -410,7 +410,7 @@ def run_native(args, rank, world, local_rank):
             "peak": round(peak_tops, 3),
             "unit": "Top/s (FP32 lane ops)",
             "frac": round(achieved_tops / peak_tops, 4),
-            "traffic": None,
+            "traffic": ncu_traffic(args.workload),
             "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {peak_mhz:.0f} MHz "
                           f"(derived from unit counts and max clock)",
             "algorithmic": f"{FP32_OPS_PER_DELAY_SUM} FP32 ops x {contributing} contributing "
@@ -430,6 +430,25 @@ def run_native(args, rank, world, local_rank):
                                     "kind": "oracle", "sample": desc,
                                     "cpu": _cpu_model(), "seconds": round(spent, 2)}
     return line
+
+
+def ncu_traffic(workload):
+    """DRAM bytes per launch of the DAS kernel from the committed ncu summary, or None.
+
+    The summary records the hash of csrc/das.cu it was captured with; a kernel
+    changed since then has no valid traffic figure.
+    """
+    import hashlib
+    prof = os.path.join(ROOT, "profiles", f"das_tiled_{workload}.md")
+    src = os.path.join(ROOT, "paper_1811_01566_gb300", "csrc", "das.cu")
+    try:
+        fields = dict(ln.split(": ", 1) for ln in open(prof).read().splitlines() if ": " in ln
+                      and ln.split(": ", 1)[0] in ("traffic_bytes_per_launch", "source_sha256"))
+        if fields.get("source_sha256") != hashlib.sha256(open(src, "rb").read()).hexdigest():
+            return None
+        return int(fields["traffic_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
 
 
 def _cpu_model():
