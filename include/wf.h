@@ -205,6 +205,36 @@ wf_status wf_logclip(const float* env, int32_t batch, int32_t nz, int32_t nx, co
                      float db_min, float db_max, float* out_db, wf_stream stream);
 
 /*
+ * STAI delay-and-sum exactly as wf_das_stai, without a caller workspace.
+ * (No counterpart in the paper: this entry point exists for callers that
+ * cannot allocate device memory, such as a real-time acquisition loop whose
+ * device memory is fixed when it starts, or a plain C host program that links
+ * only this library and has no device allocator of its own.)
+ *
+ * The split partials go to a fixed scratch array of WF_FIXED_SCRATCH_BYTES
+ * that the library keeps in device memory; every GPU that loads the library
+ * holds it until the process exits.  The call allocates and frees nothing.
+ *  - Calls whose workspace need (wf_das_workspace_bytes) exceeds
+ *    WF_FIXED_SCRATCH_BYTES return WF_ERR_WORKSPACE and launch nothing.
+ *  - The first call on a device looks up the array's device address with that
+ *    device current; make that first call before any stream capture.
+ *  - All calls on a device share the one array, which keeps the last call's
+ *    contents: calls that overlap on the GPU (different streams, or host
+ *    threads without ordering between them) race and may return wrong images.
+ *    Order such calls on one stream.
+ * Arguments, layouts and the rest of the error behaviour are those of
+ * wf_das_stai.
+ */
+#define WF_FIXED_SCRATCH_BYTES (32u << 20)
+wf_status wf_das_stai_fixed_scratch(const wf_probe* probe, const wf_grid* grid, int32_t batch,
+                                    int32_t n_tx, const int32_t* tx_elem, int32_t n_rx,
+                                    int32_t n_samples, double t_start, wf_dtype dtype,
+                                    const void* rf, float rf_scale, float* out, wf_stream stream);
+
+/* Size in bytes of the fixed scratch array behind wf_das_stai_fixed_scratch. */
+size_t wf_fixed_scratch_bytes(void);
+
+/*
  * Synchronises `stream` and reports whether a DAS kernel that used `ws`
  * recorded an internal inconsistency (WF_ERR_INTERNAL) since the workspace
  * was last handed to wf_das_stai / wf_das_pwi.  Debug aid; the only call that

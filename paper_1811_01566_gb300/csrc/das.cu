@@ -1270,3 +1270,61 @@ extern "C" wf_status wf_workspace_check(const void* ws, size_t ws_bytes, wf_stre
     if (cudaMemcpy(&h, ws, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return WF_ERR_CUDA;
     return h.flags ? WF_ERR_INTERNAL : WF_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Fixed-scratch STAI entry point: the workspace is a file-scope device array
+// instead of caller memory.  The paper has no counterpart; it serves callers
+// that cannot allocate device memory themselves.
+// ---------------------------------------------------------------------------
+namespace wf {
+namespace {
+
+constexpr size_t kFixedScratchBytes = (size_t)WF_FIXED_SCRATCH_BYTES;
+
+// Shared by every call on a device and held by each device that loads the library.
+static __device__ __align__(256) unsigned char g_fixed_scratch[kFixedScratchBytes];
+
+// Device address of g_fixed_scratch, looked up once per device with that device
+// current (in host code the symbol is only a host-side stand-in).
+constexpr int kMaxDevices = 64;
+void* g_scratch_ptr[kMaxDevices] = {};
+int g_scratch_ready[kMaxDevices] = {};
+
+wf_status fixed_scratch(void** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return WF_ERR_CUDA;
+    if (dev < 0 || dev >= kMaxDevices) return WF_ERR_UNSUPPORTED;
+    if (__atomic_load_n(&g_scratch_ready[dev], __ATOMIC_ACQUIRE)) {
+        *out = g_scratch_ptr[dev];
+        return WF_OK;
+    }
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_fixed_scratch) != cudaSuccess || !p) return WF_ERR_CUDA;
+    g_scratch_ptr[dev] = p;
+    __atomic_store_n(&g_scratch_ready[dev], 1, __ATOMIC_RELEASE);
+    *out = p;
+    return WF_OK;
+}
+
+}  // namespace
+}  // namespace wf
+
+extern "C" wf_status wf_das_stai_fixed_scratch(const wf_probe* probe, const wf_grid* grid,
+                                               int32_t batch, int32_t n_tx, const int32_t* tx_elem,
+                                               int32_t n_rx, int32_t n_samples, double t_start,
+                                               wf_dtype dtype, const void* rf, float rf_scale,
+                                               float* out, wf_stream stream) {
+    if (check_probe_grid(probe, grid) != WF_OK || batch < 1 || n_tx < 1 || n_tx > WF_MAX_TX)
+        return WF_ERR_INVALID_ARG;
+    if (dtype != WF_F32 && dtype != WF_F16 && dtype != WF_I16) return WF_ERR_INVALID_ARG;
+    if (n_samples < 1 || n_samples > WF_MAX_SAMPLES) return WF_ERR_INVALID_ARG;
+    const Plan P = make_plan(0, probe, grid, batch, n_tx, n_samples, dtype == WF_F32 ? 4 : 2);
+    if (P.ws_bytes > kFixedScratchBytes) return WF_ERR_WORKSPACE;
+    void* ws = nullptr;
+    const wf_status s = fixed_scratch(&ws);
+    if (s != WF_OK) return s;
+    return wf_das_stai(probe, grid, batch, n_tx, tx_elem, n_rx, n_samples, t_start, dtype, rf,
+                       rf_scale, out, ws, kFixedScratchBytes, stream);
+}
+
+extern "C" size_t wf_fixed_scratch_bytes(void) { return kFixedScratchBytes; }
