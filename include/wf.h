@@ -151,20 +151,22 @@ wf_status wf_das_pwi(const wf_probe* probe, const wf_grid* grid, int32_t batch,
 /*
  * Delays in samples, s(p, t, r) above, exactly as the tiled DAS kernel forms
  * them (same device code): the integer start of the staging window plus the
- * FP32 window-relative delay.  This is the check that the FP32 geometry path
- * stays within its delay-error budget.  Triples the DAS kernels never
+ * FP32 window-relative delay, returned as the two parts (no FP64 on the GPU:
+ * the caller adds them in double).  This is the check that the FP32 geometry
+ * path stays within its delay-error budget.  Triples the DAS kernels never
  * evaluate (receive element outside the pixel tile's aperture range, STAI
- * transmit element outside it) are NaN.
+ * transmit element outside it) have out_rel = NaN.
  *
  *  mode         0 = STAI (uses tx_elem, t_start[0]), 1 = PWI (angles_rad, t_start[k])
  *  n_tx         transmits or angles; tx_elem/angles_rad/t_start as above (host)
  *  n_pix, pix   device int32 [n_pix] linear pixel indices iz * nx + ix
- *  out          device double [n_pix][n_tx][n_elements]
+ *  out_lo       device int32 [n_pix][n_tx][n_elements] window start (samples)
+ *  out_rel      device float [n_pix][n_tx][n_elements] delay relative to out_lo
  */
 wf_status wf_das_delays(const wf_probe* probe, const wf_grid* grid, int32_t mode,
                         int32_t n_tx, const int32_t* tx_elem, const double* angles_rad,
-                        const double* t_start, int32_t n_pix, const int32_t* pix, double* out,
-                        wf_stream stream);
+                        const double* t_start, int32_t n_pix, const int32_t* pix, int32_t* out_lo,
+                        float* out_rel, wf_stream stream);
 
 /*
  * Envelope detection (Fig. 2 "Analytic Signal" -> "Absolute Value"; Sec.

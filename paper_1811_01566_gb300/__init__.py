@@ -75,7 +75,7 @@ def _load():
             lib.wf_das_pwi.argtypes = [P, G, i32, i32, vp, vp, i32, i32, i32, vp, f32, vp, vp, sz,
                                        vp]
             lib.wf_das_pwi.restype = C.c_int
-            lib.wf_das_delays.argtypes = [P, G, i32, i32, vp, vp, vp, i32, vp, vp, vp]
+            lib.wf_das_delays.argtypes = [P, G, i32, i32, vp, vp, vp, i32, vp, vp, vp, vp]
             lib.wf_das_delays.restype = C.c_int
             lib.wf_envelope.argtypes = [vp, i32, i32, i32, vp, vp, vp]
             lib.wf_envelope.restype = C.c_int
@@ -204,10 +204,16 @@ def das_pwi(rf: torch.Tensor, probe: Probe, grid: Grid, *, angles, t_start=None,
 
 def das_delays(probe: Probe, grid: Grid, mode: str, pix: torch.Tensor, *, n_tx: int,
                tx_elem=None, angles=None, t_start=None, stream=None) -> torch.Tensor:
-    """Delays (samples) the DAS kernels use: float64 [n_pix, n_tx, n_elements], NaN where unused."""
+    """Delays (samples) the DAS kernels use: float64 [n_pix, n_tx, n_elements], NaN where unused.
+
+    The library returns the integer window start and the FP32 window-relative
+    delay; they are added here, on the host side of the boundary, in float64.
+    """
     if not (pix.is_cuda and pix.dtype == torch.int32 and pix.is_contiguous()):
         raise ValueError("pix must be a contiguous CUDA int32 tensor")
-    out = torch.empty(pix.numel(), n_tx, probe.n_elements, device=pix.device, dtype=torch.float64)
+    shape = (pix.numel(), n_tx, probe.n_elements)
+    lo = torch.empty(shape, device=pix.device, dtype=torch.int32)
+    rel = torch.empty(shape, device=pix.device, dtype=torch.float32)
     tx = None if tx_elem is None else (C.c_int32 * n_tx)(*[int(v) for v in tx_elem])
     ang = None if angles is None else (C.c_double * n_tx)(*[float(v) for v in angles])
     if t_start is None:
@@ -217,10 +223,10 @@ def das_delays(probe: Probe, grid: Grid, mode: str, pix: torch.Tensor, *, n_tx: 
             [float(v) for v in t_start]
         ts = (C.c_double * len(vals))(*vals)
     st = _load().wf_das_delays(C.byref(probe._c()), C.byref(grid._c()), 0 if mode == "stai" else 1,
-                               int(n_tx), tx, ang, ts, pix.numel(), pix.data_ptr(), out.data_ptr(),
-                               _stream(stream))
+                               int(n_tx), tx, ang, ts, pix.numel(), pix.data_ptr(), lo.data_ptr(),
+                               rel.data_ptr(), _stream(stream))
     _check(st, "wf_das_delays")
-    return out
+    return lo.cpu().double() + rel.cpu().double()
 
 
 def envelope(bf: torch.Tensor, *, out: torch.Tensor | None = None, with_max: bool = True,

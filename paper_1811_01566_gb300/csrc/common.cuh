@@ -81,6 +81,63 @@ __device__ __forceinline__ float apod_weight(int apod, float xe, float px, float
     return fmaf(0.5f, cospif(u), 0.5f);
 }
 
+// ---------------------------------------------------------------------------
+// Double-float arithmetic: a value is the unevaluated sum hi + lo of two FP32
+// numbers (about 48 significant bits).  Built from the error-free transforms
+// TwoSum (Knuth) and TwoProd (one FMA), so reference geometry keeps FP64-like
+// accuracy without FP64 instructions.  Requires IEEE round-to-nearest FP32
+// and no reassociation (the library is compiled without fast-math).
+// ---------------------------------------------------------------------------
+struct DF {
+    float hi, lo;
+};
+
+__host__ __device__ inline DF df_from_double(double v) {
+    DF r;
+    r.hi = (float)v;
+    r.lo = (float)(v - (double)r.hi);
+    return r;
+}
+
+__device__ __forceinline__ DF two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    return DF{s, (a - (s - bb)) + (b - bb)};
+}
+
+__device__ __forceinline__ DF quick_two_sum(float a, float b) {  // |a| >= |b|
+    const float s = a + b;
+    return DF{s, b - (s - a)};
+}
+
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    const DF s = two_sum(a.hi, b.hi);
+    return quick_two_sum(s.hi, s.lo + (a.lo + b.lo));
+}
+
+__device__ __forceinline__ DF df_neg(DF a) { return DF{-a.hi, -a.lo}; }
+
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+    const float p = a.hi * b.hi;
+    const float e = fmaf(a.hi, b.hi, -p);
+    return quick_two_sum(p, e + fmaf(a.hi, b.lo, a.lo * b.hi));
+}
+
+// a + k b for a small integer k (exact as a float).
+__device__ __forceinline__ DF df_axpk(DF a, int k, DF b) {
+    return df_add(a, df_mul(DF{(float)k, 0.0f}, b));
+}
+
+// Square root of a non-negative double-float: FP32 root plus one Newton step.
+__device__ __forceinline__ DF df_sqrt(DF a) {
+    if (!(a.hi > 0.0f)) return DF{0.0f, 0.0f};
+    const float r = sqrtf(a.hi);
+    const float rr = r * r;
+    const float rre = fmaf(r, r, -rr);               // r^2 = rr + rre exactly
+    const float corr = (((a.hi - rr) - rre) + a.lo) * (0.5f / r);
+    return quick_two_sum(r, corr);
+}
+
 // Inverse half-aperture 2F / z of a pixel (0 when z <= 0: no aperture).
 __device__ __forceinline__ float aperture_kappa(const Geom& g, float pz) {
     return pz > 0.0f ? g.two_f / pz : 0.0f;

@@ -52,20 +52,20 @@ constexpr float kMagic = 12582912.0f;      // 1.5 * 2^23
 constexpr int kMagicBits = 0x4B400000;
 
 struct TxInfo {
-    double sin_d, cos_d, t0_d;  // PWI: steering; both: t0 = time of sample 0 times fs
+    DF sin, cos, t0;   // PWI steering (double-float); both: t0 = time of sample 0 times fs
     float sin_f, cos_f;
-    int e;                      // STAI: element fired
+    int e;             // STAI: element fired
     int pad;
 };
 
-// Sample-unit geometry in double (reference terms) next to the float copy in Geom.
-struct GeomD {
-    double gx0, gdx, gz0, gdz, xe0, pitch;
+// Sample-unit geometry as double-floats (reference terms) next to the float copy in Geom.
+struct GeomDF {
+    DF gx0, gdx, gz0, gdz, xe0, pitch;
 };
 
 struct DasArgs {
     Geom g;
-    GeomD gd;
+    GeomDF gd;
     int n_tx, ns;
     int tiles_x, n_slices, n_items;  // items per frame = tiles * slices
     int W;                           // staged positions per trace (shared stride)
@@ -117,21 +117,18 @@ struct Elem {
     float Rhi, Rlo, ax, g;
 };
 
-__device__ __forceinline__ double elem_R(const Elem& e) { return (double)e.Rhi + (double)e.Rlo; }
+__device__ __forceinline__ DF elem_R(const Elem& e) { return DF{e.Rhi, e.Rlo}; }
 
-// Exact-to-FP64 distance from the reference point to element e.
-__device__ __forceinline__ Elem make_elem(const DasArgs& a, double cx, double cz, int e) {
-    const double xe = fma((double)e, a.gd.pitch, a.gd.xe0);
-    const double ax = cx - xe;
-    const double r2 = fma(ax, ax, cz * cz);
-    const float rf = sqrtf((float)r2);
-    // one Newton step on top of the FP32 root: error ~1e-14 relative
-    double R = (double)rf + (double)((float)fma(-(double)rf, (double)rf, r2) * (0.5f / rf));
-    if (!(r2 > 0.0)) R = 0.0;
+// Distance from the reference point (cx, cz) to element e, in double-float
+// (relative error ~1e-13, far below the FP32 corrections added to it).
+__device__ __forceinline__ Elem make_elem(const DasArgs& a, DF cx, DF cz, int e) {
+    const DF xe = df_axpk(a.gd.xe0, e, a.gd.pitch);
+    const DF ax = df_add(cx, df_neg(xe));
+    const DF R = df_sqrt(df_add(df_mul(ax, ax), df_mul(cz, cz)));
     Elem el;
-    el.Rhi = (float)R;
-    el.Rlo = (float)(R - (double)el.Rhi);
-    el.ax = (float)ax;
+    el.Rhi = R.hi;
+    el.Rlo = R.lo;
+    el.ax = ax.hi;
     el.g = a.g.elem_weight ? __ldg(a.g.elem_weight + e) : 1.0f;
     return el;
 }
@@ -169,7 +166,7 @@ template <int MODE>
 __device__ __forceinline__ float2 pair_bounds(const Geom& g, const TxInfo& ti, int r, float xlo,
                                               float xhi, float zlo, float zhi) {
     const float xr = elem_x(g, r);
-    const float c = (float)(-ti.t0_d);
+    const float c = -ti.t0.hi;
     if (MODE == 0) {
         const float xt = elem_x(g, ti.e);
         const float xm = fminf(fmaxf(0.5f * (xt + xr), xlo), xhi);
@@ -190,11 +187,11 @@ __device__ __forceinline__ float2 pair_bounds(const Geom& g, const TxInfo& ti, i
     return make_float2(mn + c, mx + c);
 }
 
-// Transmit reference term (FP64).
+// Transmit reference term at the reference point (double-float).
 template <int MODE>
-__device__ __forceinline__ double tx_ref(const TxInfo& ti, double cx, double cz, double R_et) {
-    if (MODE == 0) return R_et - ti.t0_d;
-    return fma(cx, ti.sin_d, fma(cz, ti.cos_d, -ti.t0_d));
+__device__ __forceinline__ DF tx_ref(const TxInfo& ti, DF cx, DF cz, DF R_et) {
+    if (MODE == 0) return df_add(R_et, df_neg(ti.t0));
+    return df_add(df_add(df_mul(cx, ti.sin), df_mul(cz, ti.cos)), df_neg(ti.t0));
 }
 
 __device__ __forceinline__ void flag(WsHeader* h, unsigned bit, unsigned a, unsigned b, unsigned c) {
@@ -209,7 +206,7 @@ __device__ __forceinline__ void flag(WsHeader* h, unsigned bit, unsigned a, unsi
 // of the tile is the FP64 reference point.
 struct TileGeo {
     int ix0, iz0;
-    double cx, cz;
+    DF cx, cz;
     float xlo, xhi, zlo, zhi;
     int2 er;
 };
@@ -220,8 +217,8 @@ __device__ __forceinline__ TileGeo tile_geo(const DasArgs& a, int ix0, int iz0) 
     TileGeo t;
     t.ix0 = ix0;
     t.iz0 = iz0;
-    t.cx = fma((double)ix0, a.gd.gdx, a.gd.gx0);
-    t.cz = fma((double)iz0, a.gd.gdz, a.gd.gz0);
+    t.cx = df_axpk(a.gd.gx0, ix0, a.gd.gdx);
+    t.cz = df_axpk(a.gd.gz0, iz0, a.gd.gdz);
     t.xlo = pixel_x(g, ix0);
     t.xhi = pixel_x(g, ix0 + COLS - 1);
     t.zlo = pixel_z(g, iz0);
@@ -242,13 +239,14 @@ struct StageInfo {
     __device__ __forceinline__ int over() const { return flags >> 1; }
 };
 
-__device__ __forceinline__ StageInfo make_stage(const DasArgs& a, float mn, float mx, double txref,
-                                                double R_r0) {
+__device__ __forceinline__ StageInfo make_stage(const DasArgs& a, float mn, float mx, DF txref,
+                                                DF R_r0) {
     StageInfo si;
     si.lo = ((int)floorf(mn) - 2) & ~7;
     si.len = (((int)ceilf(mx) + 2 - si.lo + 1) + 7) & ~7;
     const int skip = (si.lo + si.len <= 0 || si.lo > a.ns - 2) ? 1 : 0;
-    si.B = (float)(txref + R_r0 - (double)si.lo);
+    const DF x = df_add(txref, R_r0);
+    si.B = (x.hi - (float)si.lo) + x.lo;   // x.hi - lo is exact: lo is an integer near x.hi
     const int over = si.len > a.W ? si.len : 0;
     if (over) si.len = a.W;
     si.flags = skip | (over << 1);
@@ -506,7 +504,7 @@ __global__ void __launch_bounds__(kThreads, 2) das_tiled_kernel(const __grid_con
     Elem* el = reinterpret_cast<Elem*>(smem_raw + L.elems);         // [E range]
     T* raw = reinterpret_cast<T*>(smem_raw + L.raw);                // [ring][kC][W + 8]
     __shared__ __align__(8) unsigned long long s_bar[kMaxRing];
-    __shared__ double s_txref[TS];
+    __shared__ DF s_txref[TS];
     __shared__ float2 s_dtw[TS][kThreads / 32];   // STAI: per-warp range of the transmit correction
     __shared__ int s_tlist[TS];
     __shared__ int s_nact;
@@ -530,8 +528,8 @@ __global__ void __launch_bounds__(kThreads, 2) das_tiled_kernel(const __grid_con
 #pragma unroll
     for (int p = 0; p < P; ++p) {
         uz[p] = (float)(lz + S::kLR * p) * g.gdz;
-        kz[p] = uz[p] * fmaf(2.0f, (float)tg.cz, uz[p]);
-        kap[p] = aperture_kappa(g, (float)tg.cz + uz[p]);
+        kz[p] = uz[p] * fmaf(2.0f, tg.cz.hi, uz[p]);
+        kap[p] = aperture_kappa(g, tg.cz.hi + uz[p]);
     }
     // Elements that can weigh on this warp's columns (all rows of the tile).
     const int2 wr = tile_elements(g, pixel_x(g, tg.ix0 + WCOL * warp),
@@ -573,7 +571,7 @@ __global__ void __launch_bounds__(kThreads, 2) das_tiled_kernel(const __grid_con
             mx = warp_max(mx);
             if (lane == 0) s_dtw[j][warp] = make_float2(mn, mx);
         }
-        if (tid == j) s_txref[j] = tx_ref<MODE>(ti, tg.cx, tg.cz, MODE == 0 ? elem_R(el[ti.e - er.x]) : 0.0);
+        if (tid == j) s_txref[j] = tx_ref<MODE>(ti, tg.cx, tg.cz, MODE == 0 ? elem_R(el[ti.e - er.x]) : DF{0.0f, 0.0f});
     }
     const int n_chunks = n_act > 0 ? (er.y - er.x + kC) / kC : 0;
     const int n_stages = n_chunks * n_act;
@@ -806,8 +804,8 @@ __global__ void das_reduce_kernel(const float* __restrict__ part, float* __restr
 }
 
 // Direct per-pixel gather for geometries whose staging windows do not fit in
-// shared memory (very coarse grids).  Delays in FP64 (this path is rare and
-// has no tile-relative reference), interpolation and sums in FP32.
+// shared memory (very coarse grids).  Each pixel is its own reference point:
+// delays in double-float, interpolation and sums in FP32.
 template <int MODE, typename T>
 __global__ void __launch_bounds__(256) das_direct_kernel(const __grid_constant__ DasArgs a) {
     const Geom& g = a.g;
@@ -816,37 +814,46 @@ __global__ void __launch_bounds__(256) das_direct_kernel(const __grid_constant__
     const int b = blockIdx.z;
     if (ix >= g.nx || iz >= g.nz) return;
     const T* rf = reinterpret_cast<const T*>(a.rf) + (long long)b * a.frame_elems;
-    const double pxd = fma((double)ix, a.gd.gdx, a.gd.gx0);
-    const double pzd = fma((double)iz, a.gd.gdz, a.gd.gz0);
-    const float px = (float)pxd, pz = (float)pzd, kap = aperture_kappa(g, pz);
-    const int2 er = tile_elements(g, px, px, pz);
+    const DF px = df_axpk(a.gd.gx0, ix, a.gd.gdx), pz = df_axpk(a.gd.gz0, iz, a.gd.gdz);
+    const DF pz2 = df_mul(pz, pz);
+    const float kap = aperture_kappa(g, pz.hi);
+    const int2 er = tile_elements(g, px.hi, px.hi, pz.hi);
+    auto dist = [&](int e, float& dxe) {
+        const DF d = df_add(df_axpk(a.gd.xe0, e, a.gd.pitch), df_neg(px));
+        dxe = d.hi;
+        return df_sqrt(df_add(df_mul(d, d), pz2));
+    };
     float acc = 0.0f;
     for (int t = 0; t < a.n_tx; ++t) {
         const TxInfo& ti = a.tx[t];
-        double dt;
+        DF dt;
         float wt;
         if (MODE == 0) {
-            const double xe = fma((double)ti.e, a.gd.pitch, a.gd.xe0);
-            dt = sqrt((pxd - xe) * (pxd - xe) + pzd * pzd) - ti.t0_d;
-            wt = apod_w(g.apod, (float)(xe - pxd), kap);
+            float dxe;
+            dt = df_add(dist(ti.e, dxe), df_neg(ti.t0));
+            wt = apod_w(g.apod, dxe, kap);
             if (g.elem_weight) wt *= __ldg(g.elem_weight + ti.e);
         } else {
-            dt = fma(pxd, ti.sin_d, fma(pzd, ti.cos_d, -ti.t0_d));
+            dt = df_add(df_add(df_mul(px, ti.sin), df_mul(pz, ti.cos)), df_neg(ti.t0));
             wt = 1.0f;
         }
         if (wt == 0.0f) continue;
         float inner = 0.0f;
         for (int r = er.x; r <= er.y; ++r) {
-            const double xe = fma((double)r, a.gd.pitch, a.gd.xe0);
-            float w = apod_w(g.apod, (float)(xe - pxd), kap);
+            float dxe;
+            const DF dr = dist(r, dxe);
+            float w = apod_w(g.apod, dxe, kap);
             if (g.elem_weight) w *= __ldg(g.elem_weight + r);
             if (w == 0.0f) continue;
-            const double s = dt + sqrt((pxd - xe) * (pxd - xe) + pzd * pzd);
-            const double fl = floor(s);
-            if (!(fl >= 0.0) || !(fl <= (double)(a.ns - 2))) continue;
+            const DF sd = df_add(dt, dr);
+            float fl = floorf(sd.hi);
+            float f = (sd.hi - fl) + sd.lo;
+            if (f < 0.0f) { fl -= 1.0f; f += 1.0f; }
+            if (f >= 1.0f) { fl += 1.0f; f -= 1.0f; }
+            if (!(fl >= 0.0f) || !(fl <= (float)(a.ns - 2))) continue;
             const T* tr = rf + ((long long)t * g.n_elements + r) * a.ns + (int)fl;
             const float x0 = raw_one<T>(raw_bits<T>(tr)), x1 = raw_one<T>(raw_bits<T>(tr + 1));
-            inner = fmaf(w, fmaf((float)(s - fl), x1 - x0, x0), inner);
+            inner = fmaf(w, fmaf(f, x1 - x0, x0), inner);
         }
         acc = fmaf(wt, inner, acc);
     }
@@ -859,7 +866,7 @@ __global__ void __launch_bounds__(256) das_direct_kernel(const __grid_constant__
 // range, inactive transmit) are NaN.
 template <int MODE, int WCOL, int P>
 __global__ void das_delays_kernel(const __grid_constant__ DasArgs a, const int32_t* __restrict__ pix,
-                                  int n_pix, double* __restrict__ out) {
+                                  int n_pix, int32_t* __restrict__ out_lo, float* __restrict__ out_rel) {
     using S = Shape<WCOL, P>;
     const Geom& g = a.g;
     const long long n = (long long)n_pix * a.n_tx * g.n_elements;
@@ -875,17 +882,18 @@ __global__ void das_delays_kernel(const __grid_constant__ DasArgs a, const int32
         const TxInfo& ti = a.tx[t];
         const int2 er = tg.er;
         if (r < er.x || r > er.y || (MODE == 0 && (ti.e < er.x || ti.e > er.y))) {
-            out[i] = __longlong_as_double(0x7ff8000000000000LL);
+            out_lo[i] = 0;
+            out_rel[i] = __int_as_float(0x7fc00000);
             continue;
         }
         const float ux = (float)(ix - tg.ix0) * g.gdx;
         const float uz = (float)(iz - tg.iz0) * g.gdz;
-        const float kz = uz * fmaf(2.0f, (float)tg.cz, uz);
+        const float kz = uz * fmaf(2.0f, tg.cz.hi, uz);
         const int r0 = er.x + ((r - er.x) / kC) * kC;
         const int r_last = min(r0 + kC - 1, er.y);
         const Elem e0 = make_elem(a, tg.cx, tg.cz, r0);
         const Elem erl = make_elem(a, tg.cx, tg.cz, r);
-        double R_et = 0.0;
+        DF R_et{0.0f, 0.0f};
         float dtx;
         if (MODE == 0) {
             const Elem et = make_elem(a, tg.cx, tg.cz, ti.e);
@@ -903,7 +911,8 @@ __global__ void das_delays_kernel(const __grid_constant__ DasArgs a, const int32
         const StageInfo si = make_stage(a, mn, mx, tx_ref<MODE>(ti, tg.cx, tg.cz, R_et), elem_R(e0));
         const float dr = elem_rel(erl, e0) + dist_delta(erl, ux, kz);
         const float s = (si.B + dtx) + dr;
-        out[i] = (double)si.lo + (double)s;
+        out_lo[i] = si.lo;
+        out_rel[i] = s;
     }
 }
 
@@ -929,6 +938,11 @@ wf_status check_probe_grid(const wf_probe* p, const wf_grid* g) {
     return WF_OK;
 }
 
+// Sample-unit geometry in host double precision.
+struct GeomD {
+    double gx0, gdx, gz0, gdz, xe0, pitch;
+};
+
 void make_geom(const wf_probe* p, const wf_grid* g, Geom& G, GeomD& D) {
     const double sc = p->fs / p->c;  // samples per metre
     D.gx0 = g->x_min * sc;
@@ -949,6 +963,17 @@ void make_geom(const wf_probe* p, const wf_grid* g, Geom& G, GeomD& D) {
     G.nz = g->nz;
     G.nx = g->nx;
     G.elem_weight = p->elem_weight;
+}
+
+void make_geom(const wf_probe* p, const wf_grid* g, Geom& G, GeomDF& F) {
+    GeomD D;
+    make_geom(p, g, G, D);
+    F.gx0 = df_from_double(D.gx0);
+    F.gdx = df_from_double(D.gdx);
+    F.gz0 = df_from_double(D.gz0);
+    F.gdz = df_from_double(D.gdz);
+    F.xe0 = df_from_double(D.xe0);
+    F.pitch = df_from_double(D.pitch);
 }
 
 // Largest |delay| (samples) any pixel/element pair can produce, for the
@@ -1161,7 +1186,7 @@ double fill_tx(DasArgs& a, const wf_probe* probe, int mode, int n_tx, const int3
         TxInfo ti{};
         const double t0 = t_start ? t_start[per_tx_start ? t : 0] : 0.0;
         if (!std::isfinite(t0)) return -1.0;
-        ti.t0_d = t0 * probe->fs;
+        ti.t0 = df_from_double(t0 * probe->fs);
         if (mode == 0) {
             const int e = tx_elem ? tx_elem[t] : t;
             if (e < 0 || e >= probe->n_elements) return -1.0;
@@ -1170,13 +1195,13 @@ double fill_tx(DasArgs& a, const wf_probe* probe, int mode, int n_tx, const int3
             const double th = angles[t];
             // steering beyond +-89 degrees has no plane wave travelling into the medium
             if (!std::isfinite(th) || std::fabs(th) > 1.5533430342749532) return -1.0;
-            ti.sin_d = std::sin(th);
-            ti.cos_d = std::cos(th);
-            ti.sin_f = (float)ti.sin_d;
-            ti.cos_f = (float)ti.cos_d;
+            ti.sin = df_from_double(std::sin(th));
+            ti.cos = df_from_double(std::cos(th));
+            ti.sin_f = ti.sin.hi;
+            ti.cos_f = ti.cos.hi;
         }
         a.tx[t] = ti;
-        extra = std::max(extra, std::fabs(ti.t0_d));
+        extra = std::max(extra, std::fabs(t0 * probe->fs));
     }
     return extra;
 }
@@ -1234,14 +1259,14 @@ extern "C" wf_status wf_das_pwi(const wf_probe* probe, const wf_grid* grid, int3
 extern "C" wf_status wf_das_delays(const wf_probe* probe, const wf_grid* grid, int32_t mode,
                                    int32_t n_tx, const int32_t* tx_elem, const double* angles_rad,
                                    const double* t_start, int32_t n_pix, const int32_t* pix,
-                                   double* out, wf_stream stream) {
+                                   int32_t* out_lo, float* out_rel, wf_stream stream) {
     thread_local DasArgs local;
     DasArgs& a = local;
     wf_status s = check_probe_grid(probe, grid);
     if (s != WF_OK) return s;
     if (mode != 0 && mode != 1) return WF_ERR_INVALID_ARG;
     if (mode == 1 && !angles_rad) return WF_ERR_INVALID_ARG;
-    if (n_tx < 1 || n_tx > WF_MAX_TX || n_pix < 0 || (n_pix > 0 && (!pix || !out)))
+    if (n_tx < 1 || n_tx > WF_MAX_TX || n_pix < 0 || (n_pix > 0 && (!pix || !out_lo || !out_rel)))
         return WF_ERR_INVALID_ARG;
     const double extra = fill_tx(a, probe, mode, n_tx, tx_elem, angles_rad, t_start, mode == 1);
     if (extra < 0.0) return WF_ERR_INVALID_ARG;
@@ -1253,11 +1278,11 @@ extern "C" wf_status wf_das_delays(const wf_probe* probe, const wf_grid* grid, i
     a.W = 1 << 30;   // and never clamps a window
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (mode == 0) {
-        if (P.cfg.p == 4) das_delays_kernel<0, 4, 4><<<304, 256, 0, st>>>(a, pix, n_pix, out);
-        else das_delays_kernel<0, 4, 2><<<304, 256, 0, st>>>(a, pix, n_pix, out);
+        if (P.cfg.p == 4) das_delays_kernel<0, 4, 4><<<304, 256, 0, st>>>(a, pix, n_pix, out_lo, out_rel);
+        else das_delays_kernel<0, 4, 2><<<304, 256, 0, st>>>(a, pix, n_pix, out_lo, out_rel);
     } else {
-        if (P.cfg.p == 4) das_delays_kernel<1, 4, 4><<<304, 256, 0, st>>>(a, pix, n_pix, out);
-        else das_delays_kernel<1, 4, 2><<<304, 256, 0, st>>>(a, pix, n_pix, out);
+        if (P.cfg.p == 4) das_delays_kernel<1, 4, 4><<<304, 256, 0, st>>>(a, pix, n_pix, out_lo, out_rel);
+        else das_delays_kernel<1, 4, 2><<<304, 256, 0, st>>>(a, pix, n_pix, out_lo, out_rel);
     }
     return last_launch_status();
 }

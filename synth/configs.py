@@ -68,13 +68,15 @@ class Case:
 
 
 def _with_rf(case: Case, rf64: np.ndarray, dtype: str) -> Case:
+    """The case with its RF stored as dtype; meta["rf_f64"] keeps the unrounded synthesis."""
+    meta = {**case.meta, "rf_f64": rf64}
     if dtype == "f32":
-        return replace(case, rf=rf64.astype(np.float32), rf_scale=1.0)
+        return replace(case, rf=rf64.astype(np.float32), rf_scale=1.0, meta=meta)
     if dtype == "f16":
-        return replace(case, rf=rf64.astype(np.float16), rf_scale=1.0)
+        return replace(case, rf=rf64.astype(np.float16), rf_scale=1.0, meta=meta)
     if dtype == "i16":
         q, s = phantom.quantise_int16(rf64)
-        return replace(case, rf=q, rf_scale=float(s))
+        return replace(case, rf=q, rf_scale=float(s), meta=meta)
     raise ValueError(dtype)
 
 

@@ -153,7 +153,7 @@ def test_fp32_delay_error_below_budget(mode):
     rng = np.random.default_rng(0)
     pix = np.concatenate([[0, nz * nx - 1, nx - 1, (nz - 1) * nx], rng.integers(0, nz * nx, 40)])
     d = wf.das_delays(pr, gr, mode, torch.tensor(pix, dtype=torch.int32, device="cuda"),
-                      n_tx=n_tx, angles=ang).cpu().numpy()
+                      n_tx=n_tx, angles=ang).numpy()
     worst, n_eval = 0.0, 0
     for q, lin in enumerate(pix):
         x, z = oracle.pixel_xz(ogr, int(lin // nx), int(lin % nx))
