@@ -42,7 +42,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--workload", default="stai_full",
-                    choices=["stai_full", "stai_small", "pwi_full_i16", "pwi_full_f16", "pwi_batch"])
+                    choices=["stai_full", "stai_small", "pwi_full_i16", "pwi_full_f16", "pwi_batch",
+                             "served"])
+    ap.add_argument("--rate", type=float, default=200.0, help="served: Poisson arrival rate (req/s)")
+    ap.add_argument("--requests", type=int, default=240, help="served: requests in the stream")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="CPU time budget of the oracle sample (cpu_baseline / reference arm)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -64,6 +67,8 @@ WORKLOAD_TEXT = {
 
 def make_case(name, device):
     from synth import configs
+    if name == "served":
+        raise ValueError("the served workload is a request stream, not a single case")
     if name == "stai_full":
         return configs.stai_full(device=device)
     if name == "stai_small":
@@ -462,6 +467,66 @@ def _cpu_model():
     return os.uname().machine
 
 
+# ----------------------------------------------------------------------------- served stream
+
+def run_served(args):
+    """Mixed STAI/PWI request stream through the continuous-batching server vs the plain
+    one-request-at-a-time FP32 path.  Throughput is taken at saturation (every request
+    queued at t = 0); latency p50/p99 under Poisson arrivals at --rate."""
+    from dataclasses import replace as dc_replace
+
+    from paper_1811_01566_gb300.serve import (CudaExecutor, Server, latency_stats,
+                                              requests_from_stream, run_sequential)
+    from synth import serving
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    shapes = serving.shape_pool(8, seed=4)
+    items = serving.stream(args.requests, args.rate, seed=4, shapes=shapes, rf_per_shape=True)
+    poisson = requests_from_stream(items)
+    burst = [dc_replace(r, arrival=0.0) for r in poisson]
+    budget = 24 << 30
+    server = Server(CudaExecutor(dev), hbm_budget=budget, max_slots_per_shape=2)
+    warm = {}
+    for r in poisson:                    # one request per shape builds its slot and graph
+        warm.setdefault(r.key(), r)
+    server.run([dc_replace(r, rid=-1 - i, arrival=0.0) for i, r in enumerate(warm.values())])
+
+    def served(reqs):
+        server.results.clear()
+        t0 = time.perf_counter()
+        res = server.run(reqs)
+        return dict(res), time.perf_counter() - t0
+
+    def sequential(reqs):
+        res = run_sequential(reqs, dev, as_float32=True)
+        return res, max(res[q.rid].latency + q.arrival for q in reqs)
+
+    sat, sat_span = served(burst)
+    lat, _ = served(poisson)
+    errors = sum(1 for r in list(sat.values()) + list(lat.values()) if r.error)
+    server.close()
+    seq_sat, seq_span = sequential(burst)
+    seq_lat, _ = sequential(poisson)
+    st, sst = latency_stats(lat), latency_stats(seq_lat)
+    n = len(poisson)
+    return {
+        "metric": "served frames/s (mixed STAI/PWI B-mode stream, int16 RF)",
+        "value": round(n / sat_span, 2), "unit": "frames/s", "n_gpus": 1,
+        "higher_is_better": True, "data": "synthetic", "dtype": "f32",
+        "config": {"workload": f"served: {len(shapes)} shapes from E in {{64,128,192}}, angles in "
+                               f"{{1,16,64}}, samples in {{1024,2048,4096}}, grids 256x256..1024x512, "
+                               f"{n} requests; throughput with all queued at t=0, latency under "
+                               f"Poisson {args.rate} req/s",
+                   "hbm_budget_bytes": budget, "slots_per_shape": 2, "launch": "CUDA graph per slot",
+                   "timing": "host wall clock from arrival to completion seen by the loop; "
+                             "includes pinned H2D of the RF and D2H of the dB image"},
+        "p50_ms": round(st["p50_ms"], 3), "p99_ms": round(st["p99_ms"], 3), "errors": errors,
+        "sequential_fp32": {"value": round(n / seq_span, 2), "unit": "frames/s",
+                            "p50_ms": round(sst["p50_ms"], 3), "p99_ms": round(sst["p99_ms"], 3)},
+        "shapes": shapes,
+    }
+
+
 # ----------------------------------------------------------------------------- reference arm
 
 def run_reference(args):
@@ -514,6 +579,10 @@ def main():
         return
     if not torch.cuda.is_available():
         raise SystemExit("bench.py: the native arm needs a CUDA GPU")
+    if args.workload == "served":
+        if rank == 0:
+            print(json.dumps(run_served(args)), flush=True)
+        return
     if world > 1:
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     try:

@@ -1,0 +1,344 @@
+"""Continuous-batching reconstruction server over libwf.
+
+The paper's goal is real-time reconstruction of a stream of acquisitions
+(abstract; Sec. I; Sec. IV).  This module serves a stream of STAI and PWI
+B-mode requests of different probe sizes, grids, angle counts and record
+lengths on one GPU:
+
+* Requests arrive at any time (``submit``); the loop admits them FIFO as soon
+  as a device slot of their shape is free, or a new slot fits in the HBM
+  budget (idle slots of other shapes are evicted, least recently used first).
+  A request that can never fit is rejected.
+* A slot is the per-shape device state kept resident between requests: the
+  RF ring slot, the DAS workspace, the image buffers, a CUDA stream and a CUDA
+  graph capturing the three-call pipeline (DAS -> envelope -> log-clip) for
+  that shape.  Delay and apodization values are recomputed inside the DAS
+  kernel from the tile's reference geometry rather than read from a stored
+  table (a table read from HBM costs more than the arithmetic on GB300).
+* Admitted requests run on their slot's stream: RF copy in (pinned host ->
+  device), graph replay, dB image copy out, completion event.  Work of
+  different requests overlaps on the device; completion is polled, never
+  waited on, so new arrivals keep being admitted while others run.
+
+Latency is measured from arrival to the moment the loop sees the completion.
+The scheduling logic is independent of CUDA: ``Server`` drives any executor
+with the ``create / launch / done / result / release`` interface, and the
+tests exercise it with a fake one on the CPU.
+"""
+from __future__ import annotations
+
+import time
+from collections import OrderedDict, deque
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class Request:
+    """One B-mode reconstruction: scan geometry + RF (pinned host tensor, int16 or float)."""
+    rid: int
+    mode: str                 # "stai" | "pwi"
+    probe: object             # paper_1811_01566_gb300.Probe
+    grid: object              # paper_1811_01566_gb300.Grid
+    rf_host: object           # torch tensor [1, n_tx, n_rx, ns], pinned
+    scan: dict = field(default_factory=dict)   # tx_elem / t_start or angles / t_start
+    rf_scale: float = 1.0
+    db_min: float = -60.0
+    db_max: float = 0.0
+    arrival: float = 0.0      # seconds on the server clock
+
+    def key(self):
+        p, g = self.probe, self.grid
+        scan = tuple(sorted((k, tuple(np.atleast_1d(v).tolist()) if v is not None else None)
+                            for k, v in self.scan.items()))
+        return (self.mode, p.n_elements, p.pitch, p.fs, p.c, p.f_number, p.apod,
+                g.nz, g.nx, g.x_min, g.x_max, g.z_min, g.z_max,
+                tuple(self.rf_host.shape), str(self.rf_host.dtype), scan, self.rf_scale,
+                self.db_min, self.db_max)
+
+
+@dataclass
+class Result:
+    rid: int
+    db: object = None         # numpy [nz, nx] dB image
+    latency: float = 0.0      # seconds, arrival -> completion seen
+    error: str | None = None
+
+
+@dataclass
+class _Slot:
+    key: tuple
+    bytes: int
+    handle: object            # executor state
+    busy: object = None       # Request in flight
+    last_used: float = 0.0
+
+
+class Server:
+    """FIFO continuous-batching loop with per-shape slots and an HBM budget."""
+
+    def __init__(self, executor, hbm_budget: int, max_slots_per_shape: int = 4,
+                 clock=time.perf_counter):
+        self.ex = executor
+        self.budget = int(hbm_budget)
+        self.max_per_shape = max_slots_per_shape
+        self.clock = clock
+        self.t0 = clock()
+        self.queue: deque[Request] = deque()
+        self.slots: list[_Slot] = []
+        self.used = 0
+        self.results: OrderedDict[int, Result] = OrderedDict()
+        self.cancelled: set[int] = set()
+
+    def now(self) -> float:
+        return self.clock() - self.t0
+
+    # -- requests -----------------------------------------------------------------
+    def submit(self, req: Request) -> None:
+        self.queue.append(req)
+
+    def cancel(self, rid: int) -> bool:
+        """Drop a request that has not started; returns False once it is on the GPU."""
+        for r in self.queue:
+            if r.rid == rid:
+                self.cancelled.add(rid)
+                return True
+        return False
+
+    # -- one pass of the loop -----------------------------------------------------
+    def step(self) -> int:
+        """Retire finished work, then admit queued requests; returns requests launched."""
+        self._retire()
+        launched = 0
+        blocked_keys = set()
+        pending = deque()
+        while self.queue:
+            req = self.queue.popleft()
+            if req.rid in self.cancelled:
+                self.cancelled.discard(req.rid)
+                self.results[req.rid] = Result(req.rid, latency=self.now() - req.arrival,
+                                               error="cancelled")
+                continue
+            key = req.key()
+            if key in blocked_keys:          # FIFO within a shape
+                pending.append(req)
+                continue
+            slot = self._slot_for(req, key)
+            if slot is None:
+                blocked_keys.add(key)
+                pending.append(req)
+                continue
+            if isinstance(slot, str):
+                self.results[req.rid] = Result(req.rid, latency=self.now() - req.arrival,
+                                               error=slot)
+                continue
+            try:
+                self.ex.launch(slot.handle, req)
+            except Exception as exc:         # a request the library rejects fails alone
+                self.results[req.rid] = Result(req.rid, latency=self.now() - req.arrival,
+                                               error=f"launch failed: {exc}")
+                continue
+            slot.busy = req
+            slot.last_used = self.now()
+            launched += 1
+        self.queue = pending
+        return launched
+
+    def _retire(self):
+        for s in self.slots:
+            if s.busy is not None and self.ex.done(s.handle):
+                req = s.busy
+                self.results[req.rid] = Result(req.rid, db=self.ex.result(s.handle),
+                                               latency=self.now() - req.arrival)
+                s.busy = None
+                s.last_used = self.now()
+
+    def _slot_for(self, req, key):
+        same = [s for s in self.slots if s.key == key]
+        for s in same:
+            if s.busy is None:
+                return s
+        if len(same) >= self.max_per_shape:
+            return None
+        try:
+            need = self.ex.footprint(req)
+        except Exception as exc:             # e.g. geometry the library refuses
+            return f"rejected: {exc}"
+        if need > self.budget:
+            return f"rejected: needs {need} bytes of device memory, budget {self.budget}"
+        while self.used + need > self.budget:
+            idle = [s for s in self.slots if s.busy is None]
+            if not idle:
+                return None
+            victim = min(idle, key=lambda s: s.last_used)
+            self.ex.release(victim.handle)
+            self.slots.remove(victim)
+            self.used -= victim.bytes
+        try:
+            handle = self.ex.create(req)
+        except Exception as exc:
+            return f"rejected: {exc}"
+        slot = _Slot(key, need, handle, last_used=self.now())
+        self.slots.append(slot)
+        self.used += need
+        return slot
+
+    # -- driving a schedule -------------------------------------------------------
+    def idle(self) -> bool:
+        return not self.queue and all(s.busy is None for s in self.slots)
+
+    def run(self, requests, poll_sleep: float = 0.0) -> OrderedDict:
+        """Feed requests at their arrival times (server clock) until all are answered."""
+        todo = deque(sorted(requests, key=lambda r: r.arrival))
+        self.t0 = self.clock()
+        while todo or not self.idle():
+            now = self.now()
+            while todo and todo[0].arrival <= now:
+                self.submit(todo.popleft())
+            self.step()
+            if poll_sleep:
+                time.sleep(poll_sleep)
+        return self.results
+
+    def close(self):
+        for s in self.slots:
+            self.ex.release(s.handle)
+        self.slots.clear()
+        self.used = 0
+
+
+def latency_stats(results) -> dict:
+    lat = np.array([r.latency for r in results.values() if r.error is None])
+    if lat.size == 0:
+        return {"p50_ms": None, "p99_ms": None, "n": 0}
+    return {"p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "n": int(lat.size)}
+
+
+class CudaExecutor:
+    """Executor over libwf on one CUDA device: slots with streams and captured graphs."""
+
+    def __init__(self, device=None, use_graphs: bool = True):
+        import torch
+
+        import paper_1811_01566_gb300 as wf
+        self.torch, self.wf = torch, wf
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else device
+        self.use_graphs = use_graphs
+
+    def footprint(self, req) -> int:
+        wf = self.wf
+        n_tx = req.rf_host.shape[1]
+        ws = wf.das_workspace_bytes(req.probe, req.grid, 1, n_tx)
+        img = req.grid.nz * req.grid.nx * 4
+        return int(req.rf_host.numel() * req.rf_host.element_size() + ws + 3 * img + 256)
+
+    def _pipeline(self, h, req):
+        wf = self.wf
+        das = wf.das_stai if req.mode == "stai" else wf.das_pwi
+        das(h["rf"], req.probe, req.grid, rf_scale=req.rf_scale, out=h["bf"], workspace=h["ws"],
+            **req.scan)
+        wf.envelope(h["bf"], out=h["env"], frame_max=h["fmax"])
+        wf.logclip(h["env"], ref=h["fmax"], db_min=req.db_min, db_max=req.db_max, out=h["db"])
+
+    def create(self, req):
+        torch, wf = self.torch, self.wf
+        dev = self.device
+        g = req.grid
+        h = {"stream": torch.cuda.Stream(device=dev)}
+        h["rf"] = torch.empty(req.rf_host.shape, dtype=req.rf_host.dtype, device=dev)
+        h["ws"] = torch.empty(wf.das_workspace_bytes(req.probe, g, 1, req.rf_host.shape[1]),
+                              dtype=torch.uint8, device=dev)
+        h["bf"] = torch.empty(1, g.nz, g.nx, device=dev)
+        h["env"] = torch.empty_like(h["bf"])
+        h["db"] = torch.empty_like(h["bf"])
+        h["fmax"] = torch.empty(1, device=dev)
+        h["out"] = torch.empty((g.nz, g.nx), dtype=torch.float32, pin_memory=True)
+        h["event"] = torch.cuda.Event()
+        h["graph"] = None
+        with torch.cuda.stream(h["stream"]):
+            h["rf"].zero_()
+            self._pipeline(h, req)          # validates the request and warms the kernels
+        h["stream"].synchronize()
+        if self.use_graphs:
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=h["stream"]):
+                self._pipeline(h, req)
+            h["graph"] = graph
+        return h
+
+    def launch(self, h, req):
+        torch = self.torch
+        with torch.cuda.stream(h["stream"]):
+            h["rf"].copy_(req.rf_host, non_blocking=True)
+            if h["graph"] is not None:
+                h["graph"].replay()
+            else:
+                self._pipeline(h, req)
+            h["out"].copy_(h["db"][0], non_blocking=True)
+            h["event"].record(h["stream"])
+
+    def done(self, h) -> bool:
+        return h["event"].query()
+
+    def result(self, h):
+        return h["out"].numpy().copy()
+
+    def release(self, h):
+        h["stream"].synchronize()
+        h.clear()
+
+
+def run_sequential(requests, device=None, as_float32: bool = True):
+    """The plain one-request-at-a-time path: each request, in arrival order, is copied in
+    (as FP32 RF when as_float32), reconstructed with eager calls and copied out before
+    the next one starts.  Returns results with latencies measured the same way."""
+    import torch
+
+    import paper_1811_01566_gb300 as wf
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else device
+    results = OrderedDict()
+    staged, converted = [], {}
+    for r in requests:   # host-side FP32 conversion happens before the clock starts
+        rf = r.rf_host
+        scale = r.rf_scale
+        if as_float32 and rf.dtype != torch.float32:
+            key = (rf.data_ptr(), scale)      # requests sharing one RF record share the copy
+            if key not in converted:
+                converted[key] = (rf.float() * scale).pin_memory()
+            rf = converted[key]
+            scale = 1.0
+        staged.append((r, rf, scale))
+    t0 = time.perf_counter()
+    for r, rf_host, scale in sorted(staged, key=lambda x: x[0].arrival):
+        while time.perf_counter() - t0 < r.arrival:
+            pass
+        rf = rf_host.to(dev, non_blocking=True)
+        das = wf.das_stai if r.mode == "stai" else wf.das_pwi
+        bf = das(rf, r.probe, r.grid, rf_scale=scale, **r.scan)
+        env, fmax = wf.envelope(bf)
+        db = wf.logclip(env, ref=fmax, db_min=r.db_min, db_max=r.db_max)
+        out = db[0].cpu().numpy()
+        results[r.rid] = Result(r.rid, db=out, latency=time.perf_counter() - t0 - r.arrival)
+    return results
+
+
+def requests_from_stream(items, pin: bool = True):
+    """Marshal stream items (dicts of numpy arrays and SI geometry) into Requests."""
+    import torch
+
+    import paper_1811_01566_gb300 as wf
+    reqs = []
+    pinned = {}
+    for it in items:
+        g = it["geometry"]
+        rf = it["rf"]
+        key = id(rf)
+        if key not in pinned:   # requests sharing one RF record share one pinned buffer
+            t = torch.from_numpy(rf)
+            pinned[key] = t.pin_memory() if pin else t
+        reqs.append(Request(it["rid"], it["shape"]["mode"], wf.Probe(**g["probe"]),
+                            wf.Grid(**g["grid"]), pinned[key], dict(g["scan"]),
+                            rf_scale=it["rf_scale"], arrival=it["arrival"]))
+    return reqs

@@ -1,0 +1,166 @@
+"""Host logic of the serving loop (admission, continuous batching, faults) with a fake GPU.
+
+The loop in paper_1811_01566_gb300.serve drives an executor; here the
+executor is a fake with a manual clock, so admission order, HBM-budget
+eviction, rejection, cancellation and failure isolation are checked on the
+CPU.  Faults are injected on the host only (a launch that raises, a request
+that does not fit); nothing here touches a GPU.
+"""
+from types import SimpleNamespace
+
+import numpy as np
+import pytest
+
+from paper_1811_01566_gb300.serve import Request, Server, latency_stats
+
+
+class Clock:
+    def __init__(self):
+        self.t = 0.0
+
+    def __call__(self):
+        return self.t
+
+
+class FakeExecutor:
+    """Each launch takes `duration` seconds of the fake clock; images are filled with the rid."""
+
+    def __init__(self, clock, duration=1.0, fail_rids=()):
+        self.clock, self.duration, self.fail = clock, duration, set(fail_rids)
+        self.created, self.released, self.launches = 0, 0, []
+
+    def footprint(self, req):
+        if req.grid.nx <= 0:
+            raise ValueError("invalid grid")
+        return req.rf_host.nbytes
+
+    def create(self, req):
+        if req.grid.nz <= 0:
+            raise ValueError("invalid grid")
+        self.created += 1
+        return {"done_at": None, "req": None}
+
+    def launch(self, h, req):
+        if req.rid in self.fail:
+            raise RuntimeError("injected launch failure")
+        h["done_at"] = self.clock() + self.duration
+        h["req"] = req
+        self.launches.append((req.rid, self.clock()))
+
+    def done(self, h):
+        return h["done_at"] is not None and self.clock() >= h["done_at"]
+
+    def result(self, h):
+        return np.full((2, 2), float(h["req"].rid))
+
+    def release(self, h):
+        self.released += 1
+
+
+def req(rid, shape=0, nbytes=10, arrival=0.0, nz=4):
+    probe = SimpleNamespace(n_elements=8 + shape, pitch=3e-4, fs=5e7, c=1540.0, f_number=1.5, apod=0)
+    grid = SimpleNamespace(nz=nz, nx=4, x_min=0.0, x_max=1e-3, z_min=1e-3, z_max=2e-3)
+    rf = np.zeros(nbytes // 2, dtype=np.int16).reshape(1, 1, 1, -1)
+    return Request(rid, "stai", probe, grid, rf, arrival=arrival)
+
+
+def drive(server, clock, until, dt=0.5):
+    while clock.t <= until:
+        server.step()
+        clock.t += dt
+
+
+def test_continuous_admission_fifo_within_shape():
+    clock = Clock()
+    ex = FakeExecutor(clock, duration=1.0)
+    s = Server(ex, hbm_budget=1000, max_slots_per_shape=2, clock=clock)
+    for i in range(3):
+        s.submit(req(i))
+    s.step()
+    assert [r for r, _ in ex.launches] == [0, 1]          # two slots of the shape
+    clock.t = 1.0
+    s.step()                                             # 0 and 1 retire, 2 is admitted
+    assert [r for r, _ in ex.launches] == [0, 1, 2]
+    assert ex.launches[2][1] == 1.0
+    clock.t = 2.0
+    s.step()
+    assert sorted(s.results) == [0, 1, 2]
+    assert s.results[2].latency == pytest.approx(2.0)
+    assert ex.created == 2
+
+
+def test_other_shapes_are_not_blocked_behind_a_busy_shape():
+    clock = Clock()
+    ex = FakeExecutor(clock, duration=5.0)
+    s = Server(ex, hbm_budget=1000, max_slots_per_shape=1, clock=clock)
+    s.submit(req(0, shape=0))
+    s.submit(req(1, shape=0))   # waits for shape 0's only slot
+    s.submit(req(2, shape=1))   # must not wait behind request 1
+    s.step()
+    assert [r for r, _ in ex.launches] == [0, 2]
+
+
+def test_hbm_budget_evicts_idle_slots_of_other_shapes():
+    clock = Clock()
+    ex = FakeExecutor(clock, duration=1.0)
+    s = Server(ex, hbm_budget=100, max_slots_per_shape=4, clock=clock)
+    s.submit(req(0, shape=0, nbytes=60))
+    s.submit(req(1, shape=1, nbytes=60))   # does not fit while shape 0 holds 60
+    s.step()
+    assert [r for r, _ in ex.launches] == [0]
+    clock.t = 1.0
+    s.step()                               # 0 retires, its idle slot is evicted, 1 runs
+    assert [r for r, _ in ex.launches] == [0, 1]
+    assert ex.released == 1
+    assert s.used <= 100
+
+
+def test_request_larger_than_budget_is_rejected_and_others_proceed():
+    clock = Clock()
+    ex = FakeExecutor(clock)
+    s = Server(ex, hbm_budget=50, clock=clock)
+    s.submit(req(0, nbytes=400))
+    s.submit(req(1, shape=1, nbytes=20))
+    s.step()
+    assert s.results[0].error.startswith("rejected")
+    assert [r for r, _ in ex.launches] == [1]
+
+
+def test_cancel_before_launch_and_failures_stay_isolated():
+    clock = Clock()
+    ex = FakeExecutor(clock, duration=1.0, fail_rids={3})
+    s = Server(ex, hbm_budget=1000, max_slots_per_shape=1, clock=clock)
+    for i in range(4):
+        s.submit(req(i))
+    s.submit(req(9, shape=2, nz=0))        # invalid geometry: create() raises
+    bad = req(8, shape=3)
+    bad.grid.nx = 0
+    s.submit(bad)                          # invalid geometry: footprint() raises
+    assert s.cancel(2)
+    s.step()
+    assert s.results[9].error.startswith("rejected")
+    assert s.results[8].error.startswith("rejected")
+    drive(s, clock, until=5.0)
+    assert s.results[2].error == "cancelled"
+    assert s.results[3].error.startswith("launch failed")
+    assert s.results[0].error is None and s.results[1].error is None
+    assert s.results[1].db[0, 0] == 1.0
+    assert not s.cancel(0)                  # already answered
+
+
+def test_run_feeds_arrivals_in_time_order_and_reports_percentiles():
+    clock = Clock()
+    ex = FakeExecutor(clock, duration=0.25)
+
+    class Ticking(Server):
+        def step(self):
+            n = super().step()
+            clock.t += 0.05
+            return n
+
+    s = Ticking(ex, hbm_budget=1000, max_slots_per_shape=2, clock=clock)
+    reqs = [req(i, arrival=0.1 * i) for i in range(20)]
+    res = s.run(reqs)
+    assert sorted(res) == list(range(20))
+    st = latency_stats(res)
+    assert st["n"] == 20 and 0.2 <= st["p50_ms"] / 1e3 <= st["p99_ms"] / 1e3 < 1.0
