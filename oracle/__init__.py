@@ -91,6 +91,11 @@ def _load():
             lib.or_frame_max.restype = C.c_double
             lib.or_logclip.argtypes = [dp, C.c_int64, C.c_double, C.c_double, C.c_double, dp]
             lib.or_logclip.restype = None
+            lib.or_window.argtypes = [P, C.c_double, C.c_double, C.c_int32]
+            lib.or_window.restype = C.c_double
+            lib.or_das_backward.argtypes = [P, G, C.c_int32, C.c_int32, ip, dp, dp, C.c_int32,
+                                            C.c_int32, dp, dp, C.c_int32, C.c_int32, dp, dp, dp]
+            lib.or_das_backward.restype = C.c_int
             _lib = lib
     return _lib
 
@@ -295,6 +300,74 @@ def logclip(env, ref=None, lo=-60.0, hi=0.0) -> np.ndarray:
     out = np.zeros_like(e)
     _load().or_logclip(_dp(e), e.size, r, lo, hi, _dp(out))
     return out
+
+
+def window(probe: Probe, x: float, z: float, e: int) -> float:
+    """Aperture window of element e at (x, z) without the element weight."""
+    ps, _w = probe._c()
+    return _load().or_window(C.byref(ps), x, z, e)
+
+
+def das_backward(rf64, probe: Probe, grid: Grid, y, *, mode: str, tx_elem=None, t_start=0.0,
+                 angles=None, t_starts=None, rows=None, threads: int = 1, need=("rf", "g", "c")):
+    """Reverse-mode derivatives of one frame's DAS for the cotangent y [nz][nx].
+
+    Returns (grad_rf [n_tx][n_rx][ns] or None, grad_g [E] or None, grad_c or None):
+    d<y, b>/d rf, d<y, b>/d g_e and d<y, b>/d c (per m/s).  Row ranges run on a
+    thread pool into private outputs that are summed afterwards.
+    """
+    lib = _load()
+    rf = _f64(rf64)
+    yy = _f64(y)
+    n_tx, n_rx, ns = rf.shape
+    ps, _w = probe._c()
+    g = grid._c()
+    m = 0 if mode == "stai" else 1
+    tx = None if tx_elem is None else np.ascontiguousarray(tx_elem, dtype=np.int32)
+    txp = tx.ctypes.data_as(C.POINTER(C.c_int32)) if tx is not None else C.POINTER(C.c_int32)()
+    if m == 0:
+        ang = np.zeros(1)
+        ts = _f64([t_start])
+    else:
+        ang = _f64(angles)
+        ts = _f64(np.zeros(n_tx) if t_starts is None else t_starts)
+    null = C.POINTER(C.c_double)()
+
+    def run(ab):
+        grf = np.zeros(rf.shape) if "rf" in need else None
+        gg = np.zeros(probe.n_elements) if "g" in need else None
+        gc = np.zeros(1) if "c" in need else None
+        rc = lib.or_das_backward(C.byref(ps), C.byref(g), m, n_tx, txp, _dp(ang), _dp(ts), n_rx,
+                                 ns, _dp(rf), _dp(yy), ab[0], ab[1],
+                                 _dp(grf) if grf is not None else null,
+                                 _dp(gg) if gg is not None else null,
+                                 _dp(gc) if gc is not None else null)
+        if rc:
+            raise ValueError("oracle das_backward: n_rx must equal n_elements")
+        return grf, gg, gc
+
+    chunks = _row_chunks(grid.nz, rows, threads)
+    if len(chunks) == 1:
+        parts = [run(chunks[0])]
+    else:
+        with ThreadPoolExecutor(len(chunks)) as ex:
+            parts = list(ex.map(run, chunks))
+
+    def total(i):
+        return None if parts[0][i] is None else sum(p[i] for p in parts)
+
+    gc = total(2)
+    return total(0), total(1), None if gc is None else float(gc[0])
+
+
+def das_backward_case(case, y, frame: int = 0, threads: int = 1, need=("rf", "g", "c")):
+    """das_backward for one frame of a ``synth.configs.Case``."""
+    pr, gr = probe_grid(case)
+    if case.mode == "stai":
+        return das_backward(case.rf64[frame], pr, gr, y, mode="stai", tx_elem=case.tx_elem,
+                            t_start=case.t_start, threads=threads, need=need)
+    return das_backward(case.rf64[frame], pr, gr, y, mode="pwi", angles=case.angles,
+                        t_starts=case.t_starts, threads=threads, need=need)
 
 
 def das(case, frame: int = 0, threads: int = 1, rows=None) -> np.ndarray:

@@ -202,6 +202,91 @@ int or_das_pwi(const or_probe* p, const or_grid* g, int32_t n_ang, const double*
 }
 
 /*
+ * Aperture window of element e for the pixel (x, z) without the element
+ * weight: or_apod / g_e, defined also where g_e = 0 (the derivative of the
+ * beamformed value with respect to g_e needs it there).
+ */
+double or_window(const or_probe* p, double x, double z, int32_t e)
+{
+    if (p->apod == OR_NONE) return 1.0;
+    double half_width = 0.5 * z / p->f_number;
+    if (!(half_width > 0.0)) return 0.0;
+    double u = (or_element_x(p, e) - x) / half_width;
+    if (!(fabs(u) < 1.0)) return 0.0;
+    if (p->apod == OR_RECT) return 1.0;
+    return 0.5 + 0.5 * cos(M_PI * u);
+}
+
+/*
+ * Reverse-mode derivatives of delay-and-sum, for a cotangent y[nz][nx] of the
+ * beamformed image b (the differentiable beamformer that lets DAS sit inside a
+ * learned pipeline, Sec. I and Sec. IV).  Plain definition, term by term: for
+ * every (pixel p, transmit t, receive r) with both windows non-zero, the
+ * weight W = w_t w_r (STAI; w = g_e window) or W = w_r (PWI), the delay s, its
+ * floor i and fraction f, and when 0 <= i and i + 1 <= ns - 1:
+ *   grad_rf[t][r][i] += y(p) W (1 - f),  grad_rf[t][r][i+1] += y(p) W f
+ *       (the transpose of the linear interpolation);
+ *   grad_g[e] += y(p) dW/dg_e lerp  (STAI: e_t and r; PWI: r);
+ *   grad_c    += y(p) W (tr[i+1] - tr[i]) ds/dc,  ds/dc = -(s + t_start fs) / c
+ *       (s + t_start fs is the path length in samples, proportional to 1/c;
+ *        the slope is that of the segment s lies on; the windows do not
+ *        depend on c).
+ * mode 0 = STAI (tx_elem, t_start[0]), 1 = PWI (angles, t_start[k]).
+ * Pixel rows [row_begin, row_end) only; every output accumulates (+=), so
+ * callers zero them once and may split rows.  Any output may be NULL.
+ */
+int or_das_backward(const or_probe* p, const or_grid* g, int32_t mode, int32_t n_tx,
+                    const int32_t* tx_elem, const double* angles, const double* t_start,
+                    int32_t n_rx, int32_t ns, const double* rf, const double* y,
+                    int32_t row_begin, int32_t row_end, double* grad_rf, double* grad_g,
+                    double* grad_c)
+{
+    if (n_rx != p->n_elements) return 1;
+    for (int32_t iz = row_begin; iz < row_end; ++iz) {
+        double z = or_pixel_z(g, iz);
+        for (int32_t ix = 0; ix < g->nx; ++ix) {
+            double x = or_pixel_x(g, ix);
+            double yp = y[(size_t)iz * g->nx + ix];
+            for (int32_t t = 0; t < n_tx; ++t) {
+                int32_t et = mode == 0 ? (tx_elem ? tx_elem[t] : t) : -1;
+                double t0 = t_start ? t_start[mode == 0 ? 0 : t] : 0.0;
+                double at = mode == 0 ? or_window(p, x, z, et) : 1.0;
+                double gt = mode == 0 && p->elem_weight ? p->elem_weight[et] : 1.0;
+                if (at == 0.0) continue;
+                for (int32_t r = 0; r < n_rx; ++r) {
+                    double ar = or_window(p, x, z, r);
+                    if (ar == 0.0) continue;
+                    double gr = p->elem_weight ? p->elem_weight[r] : 1.0;
+                    double s = mode == 0 ? or_delay_stai(p, x, z, et, r, t0)
+                                         : or_delay_pwi(p, x, z, angles[t], r, t0);
+                    double fi = floor(s);
+                    if (!(fi >= 0.0) || !(fi + 1.0 <= (double)(ns - 1))) continue;
+                    int64_t i = (int64_t)fi;
+                    double f = s - fi;
+                    size_t base = ((size_t)t * n_rx + r) * (size_t)ns;
+                    const double* tr = rf + base;
+                    double v = or_lerp(tr, ns, s);
+                    double W = gt * at * gr * ar;
+                    if (grad_rf) {
+                        grad_rf[base + i] += yp * W * (1.0 - f);
+                        grad_rf[base + i + 1] += yp * W * f;
+                    }
+                    if (grad_g) {
+                        if (mode == 0) grad_g[et] += yp * at * gr * ar * v;
+                        grad_g[r] += yp * gt * at * ar * v;
+                    }
+                    if (grad_c) {
+                        double dsdc = -(s + t0 * p->fs) / p->c;
+                        *grad_c += yp * W * (tr[i + 1] - tr[i]) * dsdc;
+                    }
+                }
+            }
+        }
+    }
+    return 0;
+}
+
+/*
  * Direct O(N^2) discrete Fourier transform (textbook definition):
  *   forward  X[k] = sum_n x[n] exp(-2 pi i k n / N)
  *   inverse  x[n] = (1/N) sum_k X[k] exp(+2 pi i k n / N)

@@ -12,6 +12,7 @@ import subprocess
 import pytest
 
 import oracle
+import test_oracle_grad_pins as grad_pins
 import test_oracle_pins as pins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "oracle.c")
@@ -40,10 +41,42 @@ MUTANTS = {
                          ["test_bin_centred_cosine_has_unit_envelope"]),
     "inverse_scale": ("if (inverse) { ar /= n; ai /= n; }", "", ["test_dft_matches_numpy_fft"]),
     "natural_log": ("20.0 * log10(e / ref)", "20.0 * log(e / ref)", ["test_logclip_closed_forms"]),
+    # reverse-mode derivatives
+    "adjoint_fraction_swapped": ("grad_rf[base + i] += yp * W * (1.0 - f);",
+                                 "grad_rf[base + i] += yp * W * f;",
+                                 ["test_adjoint_identity", "test_single_term_by_hand"]),
+    "adjoint_wrong_sample": ("grad_rf[base + i + 1] += yp * W * f;",
+                             "grad_rf[base + i] += yp * W * f;", ["test_adjoint_identity"]),
+    "grad_g_tx_term_dropped": ("if (mode == 0) grad_g[et] += yp * at * gr * ar * v;", "",
+                               ["test_weight_gradient_matches_central_difference"]),
+    "grad_g_skips_zero_weight": ("if (ar == 0.0) continue;",
+                                 "if (ar == 0.0 || (p->elem_weight && p->elem_weight[r] == 0.0)) continue;",
+                                 ["test_weight_gradient_matches_central_difference"]),
+    "grad_c_sign": ("double dsdc = -(s + t0 * p->fs) / p->c;", "double dsdc = (s + t0 * p->fs) / p->c;",
+                    ["test_sound_speed_gradient_matches_central_difference", "test_single_term_by_hand"]),
+    "grad_c_t_start_dropped": ("double dsdc = -(s + t0 * p->fs) / p->c;", "double dsdc = -s / p->c;",
+                               ["test_sound_speed_gradient_matches_central_difference",
+                                "test_single_term_by_hand"]),
+    "window_width": ("double half_width = 0.5 * z / p->f_number;", "double half_width = z / p->f_number;",
+                     ["test_window_is_apod_without_weight", "test_adjoint_identity"]),
 }
 
 
 def _call(name, golden):
+    if hasattr(grad_pins, name):
+        fn = getattr(grad_pins, name)
+        if "k" in fn.__code__.co_varnames[: fn.__code__.co_argcount]:
+            failures = []
+            for k in range(len(grad_pins.CASES)):   # every case; any failure counts
+                try:
+                    fn(k=k)
+                except AssertionError as e:
+                    failures.append(e)
+            if failures:
+                raise failures[0]
+            return
+        fn()
+        return
     fn = getattr(pins, name)
     params = {"test_bin_centred_cosine_has_unit_envelope": {"n": 64, "k0": 5},
               "test_dft_matches_numpy_fft": {"n": 16}}.get(name, {})
