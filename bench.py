@@ -440,12 +440,12 @@ def run_native(args, rank, world, local_rank):
 def ncu_traffic(workload):
     """DRAM bytes per launch of the DAS kernel from the committed ncu summary, or None.
 
-    The summary records the hash of csrc/das.cu it was captured with; a kernel
-    changed since then has no valid traffic figure.
+    The summary records the hash of csrc/das_kernels.cuh (the kernel source) it
+    was captured with; a kernel changed since then has no valid traffic figure.
     """
     import hashlib
     prof = os.path.join(ROOT, "profiles", f"das_tiled_{workload}.md")
-    src = os.path.join(ROOT, "paper_1811_01566_gb300", "csrc", "das.cu")
+    src = os.path.join(ROOT, "paper_1811_01566_gb300", "csrc", "das_kernels.cuh")
     try:
         fields = dict(ln.split(": ", 1) for ln in open(prof).read().splitlines() if ": " in ln
                       and ln.split(": ", 1)[0] in ("traffic_bytes_per_launch", "source_sha256"))

@@ -169,6 +169,38 @@ wf_status wf_das_delays(const wf_probe* probe, const wf_grid* grid, int32_t mode
                         float* out_rel, wf_stream stream);
 
 /*
+ * Reverse-mode delay-and-sum (a differentiable beamformer: DAS inside a
+ * learned pipeline, the use Sec. I and Sec. IV of the paper point to).  For a
+ * cotangent y = grad_out of the beamformed image b of wf_das_stai (mode 0) or
+ * wf_das_pwi (mode 1), the derivatives of L = sum_p y(p) b(p) with respect to
+ *
+ *   the RF:       dL/drf[t][r][i] = sum over terms of y W (1 - f) at i = floor(s)
+ *                 and y W f at i + 1 (the transpose of the interpolation),
+ *   the weights:  dL/dg_e (probe->elem_weight, both transmit and receive ends
+ *                 for STAI), summed over the batch,
+ *   sound speed:  dL/dc in 1/(m/s), through ds/dc = -(s + t_start fs) / c; the
+ *                 apodization windows depend on geometry only,
+ *
+ * W the term's weight (w_t w_r for STAI, w_r for PWI), same terms, delays and
+ * interpolation as the forward call.  Float32 RF only.  Accumulation uses
+ * float atomics, so the last bits of a result depend on scheduling.
+ *
+ *  mode, n_tx, tx_elem, angles_rad, t_start   as wf_das_delays (host arrays)
+ *  batch, n_rx, n_samples                     as wf_das_stai
+ *  rf           device float [batch][n_tx][n_rx][n_samples], 16-byte aligned
+ *  grad_out     device float [batch][nz][nx]
+ *  grad_rf      device float, rf's shape, or NULL (not computed); overwritten
+ *  grad_weight  device float [n_elements] or NULL; overwritten
+ *  grad_c       device float [1] or NULL; overwritten
+ *  stream       CUDA stream; no workspace is needed
+ */
+wf_status wf_das_backward(const wf_probe* probe, const wf_grid* grid, int32_t mode,
+                          int32_t batch, int32_t n_tx, const int32_t* tx_elem,
+                          const double* angles_rad, const double* t_start, int32_t n_rx,
+                          int32_t n_samples, const float* rf, const float* grad_out,
+                          float* grad_rf, float* grad_weight, float* grad_c, wf_stream stream);
+
+/*
  * Envelope detection (Fig. 2 "Analytic Signal" -> "Absolute Value"; Sec.
  * II-B: Hilbert transform through the FFT).  For every column x of every
  * frame, with N = nz:

@@ -12,6 +12,7 @@ Adjustment); ``bmode`` chains the three.
 from __future__ import annotations
 
 import ctypes as C
+import dataclasses
 import os
 import threading
 from dataclasses import dataclass
@@ -21,8 +22,8 @@ import torch
 from . import _build
 
 __all__ = ["Probe", "Grid", "WfError", "HANN", "RECT", "NONE", "das_stai", "das_pwi",
-           "das_workspace_bytes", "das_delays", "envelope", "logclip", "bmode",
-           "workspace_check", "library_path", "version"]
+           "das_workspace_bytes", "das_delays", "das_backward", "das", "envelope", "logclip",
+           "bmode", "workspace_check", "library_path", "version"]
 
 HANN, RECT, NONE = 0, 1, 2
 _DTYPES = {torch.float32: 0, torch.float16: 1, torch.int16: 2}
@@ -77,6 +78,9 @@ def _load():
             lib.wf_das_pwi.restype = C.c_int
             lib.wf_das_delays.argtypes = [P, G, i32, i32, vp, vp, vp, i32, vp, vp, vp, vp]
             lib.wf_das_delays.restype = C.c_int
+            lib.wf_das_backward.argtypes = [P, G, i32, i32, i32, vp, vp, vp, i32, i32, vp, vp, vp,
+                                            vp, vp, vp]
+            lib.wf_das_backward.restype = C.c_int
             lib.wf_envelope.argtypes = [vp, i32, i32, i32, vp, vp, vp]
             lib.wf_envelope.restype = C.c_int
             lib.wf_logclip.argtypes = [vp, i32, i32, i32, vp, f32, f32, vp, vp]
@@ -227,6 +231,87 @@ def das_delays(probe: Probe, grid: Grid, mode: str, pix: torch.Tensor, *, n_tx: 
                                rel.data_ptr(), _stream(stream))
     _check(st, "wf_das_delays")
     return lo.cpu().double() + rel.cpu().double()
+
+
+def das_backward(rf: torch.Tensor, grad_out: torch.Tensor, probe: Probe, grid: Grid, mode: str, *,
+                 tx_elem=None, t_start=None, angles=None, need_rf: bool = True,
+                 need_weight: bool = True, need_c: bool = True, stream=None):
+    """Reverse-mode DAS (wf_das_backward) for float32 RF [batch, n_tx, n_rx, ns].
+
+    Returns (grad_rf, grad_weight, grad_c): the derivatives of
+    sum(grad_out * DAS(rf)) with respect to the RF (same shape), the element
+    weights ([n_elements], summed over the batch) and the speed of sound
+    ([1], per m/s); an output not asked for is None.
+    """
+    rf = _as_frames(rf)
+    if rf.dtype != torch.float32:
+        raise ValueError("das_backward takes float32 RF")
+    b, n_tx, n_rx, ns = rf.shape
+    if grad_out.dim() == 2:
+        grad_out = grad_out.unsqueeze(0)
+    if not (grad_out.is_cuda and grad_out.dtype == torch.float32 and grad_out.is_contiguous()
+            and tuple(grad_out.shape) == (b, grid.nz, grid.nx)):
+        raise ValueError("grad_out must be a contiguous CUDA float32 [batch, nz, nx] tensor")
+    grf = torch.empty_like(rf) if need_rf else None
+    gw = torch.empty(probe.n_elements, device=rf.device, dtype=torch.float32) if need_weight else None
+    gc = torch.empty(1, device=rf.device, dtype=torch.float32) if need_c else None
+    if mode == "stai":
+        m, ang = 0, None
+        tx = None if tx_elem is None else (C.c_int32 * n_tx)(*[int(v) for v in tx_elem])
+        ts = (C.c_double * 1)(float(t_start or 0.0))
+    elif mode == "pwi":
+        m, tx = 1, None
+        ang = (C.c_double * n_tx)(*[float(v) for v in angles])
+        ts = None if t_start is None else (C.c_double * n_tx)(*[float(v) for v in t_start])
+    else:
+        raise ValueError("mode must be 'stai' or 'pwi'")
+
+    def ptr(t):
+        return None if t is None else t.data_ptr()
+
+    st = _load().wf_das_backward(C.byref(probe._c()), C.byref(grid._c()), m, b, n_tx, tx, ang, ts,
+                                 n_rx, ns, rf.data_ptr(), grad_out.data_ptr(), ptr(grf), ptr(gw),
+                                 ptr(gc), _stream(stream))
+    _check(st, "wf_das_backward")
+    return grf, gw, gc
+
+
+class _DelayAndSum(torch.autograd.Function):
+    """DAS as an autograd node: forward wf_das_stai / wf_das_pwi, backward wf_das_backward."""
+
+    @staticmethod
+    def forward(ctx, rf, elem_weight, c, probe, grid, mode, scan):
+        cval = float(c.detach().reshape(()).item()) if isinstance(c, torch.Tensor) else float(c)
+        w = None if elem_weight is None else elem_weight.detach().contiguous()
+        p = dataclasses.replace(probe, c=cval, elem_weight=w)
+        fwd = das_stai if mode == "stai" else das_pwi
+        out = fwd(rf, p, grid, **scan)
+        ctx.save_for_backward(rf)
+        ctx.probe, ctx.grid, ctx.mode, ctx.scan = p, grid, mode, scan
+        ctx.c_shape = c.shape if isinstance(c, torch.Tensor) else None
+        return out
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        (rf,) = ctx.saved_tensors
+        need_rf, need_w, need_c = ctx.needs_input_grad[:3]
+        scan = dict(ctx.scan)
+        grf, gw, gc = das_backward(rf, grad_out.contiguous(), ctx.probe, ctx.grid, ctx.mode,
+                                   need_rf=need_rf, need_weight=need_w, need_c=need_c, **scan)
+        if gc is not None and ctx.c_shape is not None:
+            gc = gc.reshape(ctx.c_shape)
+        return grf, gw, gc, None, None, None, None
+
+
+def das(rf: torch.Tensor, probe: Probe, grid: Grid, mode: str, *, elem_weight=None, c=None,
+        **scan) -> torch.Tensor:
+    """Differentiable delay-and-sum of float32 RF -> [batch, nz, nx].
+
+    Gradients flow to ``rf``, to ``elem_weight`` (CUDA float32 [n_elements]) and
+    to ``c`` (a CUDA scalar tensor, speed of sound in m/s) when they require
+    grad; ``scan`` is tx_elem / t_start (STAI) or angles / t_start (PWI).
+    """
+    return _DelayAndSum.apply(rf, elem_weight, probe.c if c is None else c, probe, grid, mode, scan)
 
 
 def envelope(bf: torch.Tensor, *, out: torch.Tensor | None = None, with_max: bool = True,

@@ -64,23 +64,6 @@ __device__ __forceinline__ float pixel_x(const Geom& g, int ix) { return fmaf((f
 __device__ __forceinline__ float pixel_z(const Geom& g, int iz) { return fmaf((float)iz, g.gdz, g.gz0); }
 __device__ __forceinline__ float elem_x(const Geom& g, int e) { return fmaf((float)e, g.pitch, g.xe0); }
 
-// One-way element-to-pixel distance (samples); z2 = z * z of the pixel.
-__device__ __forceinline__ float elem_dist(float xe, float px, float z2) {
-    float dx = xe - px;
-    return __fsqrt_rn(fmaf(dx, dx, z2));
-}
-
-// Receive/transmit apodization of the element at xe for a pixel with
-// inverse half-aperture kap = 2F / z (kap <= 0 or non-finite: no aperture).
-// Hann: 0.5 (1 + cos(pi u)) for |u| < 1; rect: 1 for |u| < 1; none: 1.
-__device__ __forceinline__ float apod_weight(int apod, float xe, float px, float kap) {
-    if (apod == WF_APOD_NONE) return 1.0f;
-    float u = (xe - px) * kap;
-    if (!(kap > 0.0f) || !(fabsf(u) < 1.0f)) return 0.0f;
-    if (apod == WF_APOD_RECT) return 1.0f;
-    return fmaf(0.5f, cospif(u), 0.5f);
-}
-
 // ---------------------------------------------------------------------------
 // Double-float arithmetic: a value is the unevaluated sum hi + lo of two FP32
 // numbers (about 48 significant bits).  Built from the error-free transforms

@@ -1,0 +1,465 @@
+// Reverse-mode delay-and-sum: derivatives of L = <y, b> for a cotangent y of
+// the beamformed image b = DAS(rf; g, c) (a differentiable beamformer, the use
+// the paper motivates for learned pipelines, Sec. I and Sec. IV).
+//
+// For every term (pixel p, transmit t, receive r) of the forward sum, with
+// weight W = w_t w_r (STAI; w_e = a_e g_e, a the aperture window) or W = w_r
+// (PWI), delay s, floor i, fraction f and 0 <= i <= ns - 2:
+//   dL/d rf[t][r][i] += y W (1 - f),   dL/d rf[t][r][i+1] += y W f
+//   dL/d g_e        += y (dW/dg_e) lerp          (STAI: e_t and r; PWI: r)
+//   dL/d c          += y W (rf[i+1] - rf[i]) ds/dc,  ds/dc = -(s + t0 fs) / c
+// (the windows depend on the geometry only, not on c).
+//
+// GB300 layout: the forward kernel's tiling (tile = reference point of the
+// tile-relative geometry, receive chunks of 8, one group of chunks per CTA,
+// every transmit per chunk, reciprocal STAI pairs when every element fires in
+// order).  Per stage the RF window is staged as FP32 (value, slope) pairs (the
+// slope is dlerp/ds); the interpolation transpose is accumulated with
+// shared-memory atomics into a window of the same shape and flushed once per
+// stage with global atomics (to both traces of a reciprocal pair).  Weight and
+// sound-speed sums are reduced per warp, per CTA and then globally.  Global
+// float atomics make the summation order (and so the last bits) run-dependent.
+#include "das_kernels.cuh"
+
+namespace wf {
+
+constexpr int kBwdWCOL = 4;
+constexpr int kBwdP = 2;   // tile 32 x 16 pixels: three weight sets per chunk stay in registers
+
+struct BwdSmem {
+    size_t pairs, gwin, table, elems, ge, total;
+};
+
+__host__ __device__ inline BwdSmem bwd_smem_layout(int W, int n_elements, bool need_rf) {
+    BwdSmem L;
+    size_t off = 0;
+    L.pairs = off;
+    off += (size_t)kC * W * sizeof(float2);
+    L.gwin = off;
+    off += need_rf ? (size_t)kC * (W + 8) * sizeof(float) : 0;
+    L.table = off;
+    off += (size_t)kTableStages * sizeof(StageInfo);
+    L.elems = off;
+    off += (((size_t)n_elements * sizeof(Elem)) + 15) & ~(size_t)15;
+    L.ge = off;
+    off += (((size_t)n_elements * sizeof(float)) + 15) & ~(size_t)15;
+    L.total = off;
+    return L;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int MODE, bool SYM, bool NEED_RF, bool NEED_PAR>
+__global__ void __launch_bounds__(kThreads, 2) das_backward_kernel(const __grid_constant__ DasArgs a) {
+    static_assert(!SYM || MODE == 0, "reciprocal pairing is an STAI property");
+    constexpr int WCOL = kBwdWCOL, P = kBwdP;
+    using S = Shape<WCOL, P>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const BwdSmem L = bwd_smem_layout(a.W, a.g.n_elements, NEED_RF);
+    float2* buf = reinterpret_cast<float2*>(smem_raw + L.pairs);   // [kC][W] (value, slope)
+    float* gw = reinterpret_cast<float*>(smem_raw + L.gwin);       // [kC][W + 8] RF cotangent window
+    StageInfo* st = reinterpret_cast<StageInfo*>(smem_raw + L.table);
+    Elem* el = reinterpret_cast<Elem*>(smem_raw + L.elems);        // [E range]
+    float* ge = reinterpret_cast<float*>(smem_raw + L.ge);         // [E range] weight-gradient partials
+    __shared__ int s_tlist[WF_MAX_TX];
+    __shared__ int s_info[4];
+    __shared__ float s_red[kThreads / 32];
+
+    const Geom& g = a.g;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int lx = lane % WCOL, lz = lane / WCOL;
+    const int item = blockIdx.x, b = blockIdx.y;
+    const int group = item % a.n_groups, rank = item / a.n_groups;
+    const int tzi = a.tiles_z - 1 - rank / a.tiles_x, txi = rank % a.tiles_x;
+    const TileGeo tg = tile_geo<S::kCols, S::kRows>(a, txi * S::kCols, tzi * S::kRows);
+    const float* rf = reinterpret_cast<const float*>(a.rf) + (long long)b * a.frame_elems;
+    float* grf = NEED_RF ? a.grad_rf + (long long)b * a.frame_elems : nullptr;
+    const bool vec_ok = (a.ns & 7) == 0;
+    const int GW = a.W + 8;   // cotangent window row stride
+    const long long E = g.n_elements;
+
+    const int col = WCOL * warp + lx;
+    const float ux = (float)col * g.gdx;
+    float kz[P], kap[P], uz[P], y[P];
+    const float* yb = a.grad_out + (long long)b * g.nz * g.nx;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        uz[p] = (float)(lz + S::kLR * p) * g.gdz;
+        kz[p] = uz[p] * fmaf(2.0f, tg.cz.hi, uz[p]);
+        kap[p] = aperture_kappa(g, tg.cz.hi + uz[p]);
+        const int ix = tg.ix0 + col, iz = tg.iz0 + lz + S::kLR * p;
+        y[p] = (ix < g.nx && iz < g.nz) ? __ldg(yb + (long long)iz * g.nx + ix) : 0.0f;
+    }
+    const int2 wr = tile_elements(g, pixel_x(g, tg.ix0 + WCOL * warp),
+                                  pixel_x(g, tg.ix0 + WCOL * warp + WCOL - 1), tg.zhi);
+    const int2 er = tg.er;
+    const int n_e = er.y >= er.x ? er.y - er.x + 1 : 0;
+    const int nc = (n_e + kC - 1) / kC;
+    for (int e = er.x + tid; e <= er.y; e += kThreads) {
+        el[e - er.x] = make_elem(a, tg.cx, tg.cz, e);
+        ge[e - er.x] = 0.0f;
+    }
+    if (NEED_RF)
+        for (int i = tid; i < kC * GW; i += kThreads) gw[i] = 0.0f;
+    if (tid == 0) {
+        int n = 0;
+        if (!SYM && n_e > 0)
+            for (int t = 0; t < a.n_tx; ++t) {
+                if (MODE == 0 && (a.tx[t].e < er.x || a.tx[t].e > er.y)) continue;
+                s_tlist[n++] = t;
+            }
+        const int G = a.n_groups;
+        int ka, kb, q0 = 0;
+        if (SYM) {
+            const long long total = sym_prefix(nc, nc, n_e);
+            ka = 0;
+            while (ka < nc && (long long)sym_prefix(ka, nc, n_e) * G < (long long)group * total) ++ka;
+            kb = ka;
+            while (kb < nc && (long long)sym_prefix(kb, nc, n_e) * G < (long long)(group + 1) * total) ++kb;
+            q0 = sym_prefix(ka, nc, n_e);
+        } else {
+            ka = (group * nc) / G;
+            kb = ((group + 1) * nc) / G;
+        }
+        s_info[0] = n;
+        s_info[1] = ka;
+        s_info[2] = kb;
+        s_info[3] = q0;
+    }
+    __syncthreads();
+    const int n_act = s_info[0], k_a = s_info[1], k_b = s_info[2], q0 = s_info[3];
+    const int n_stages = n_e == 0 ? 0 : SYM ? sym_prefix(k_b, nc, n_e) - q0 : (k_b - k_a) * n_act;
+
+    auto locate = [&](int q, int& k, int& j) {
+        if (SYM) {
+            const int qg = q0 + q;
+            k = sym_chunk(qg, nc);
+            j = qg - 4 * k * (k + 1);
+        } else {
+            k = k_a + q / n_act;
+            j = q - (q / n_act) * n_act;
+        }
+    };
+    auto tx_of = [&](int j) { return SYM ? er.x + j : s_tlist[j]; };
+    auto advance = [&](int& k, int& j) {
+        if (++j == (SYM ? min(kC * (k + 1), n_e) : n_act)) {
+            j = 0;
+            ++k;
+        }
+    };
+    auto fill_table = [&](int base) {
+        const int q = base + tid;
+        if (tid < kTableBatch && q < n_stages) {
+            int k, j;
+            locate(q, k, j);
+            const int t = tx_of(j);
+            const int rr0 = er.x + k * kC, rrl = min(rr0 + kC - 1, er.y);
+            const TxInfo& ti = a.tx[t];
+            float mn = 3.0e38f, mx = -3.0e38f;
+            for (int rr = SYM ? max(rr0, t) : rr0; rr <= rrl; ++rr) {
+                const float2 bd = pair_bounds<MODE>(g, ti, rr, tg.xlo, tg.xhi, tg.zlo, tg.zhi);
+                mn = fminf(mn, bd.x);
+                mx = fmaxf(mx, bd.y);
+            }
+            const DF txref = tx_ref<MODE>(ti, tg.cx, tg.cz,
+                                          MODE == 0 ? elem_R(el[ti.e - er.x]) : DF{0.0f, 0.0f});
+            st[q & (kTableStages - 1)] = make_stage(a, mn, mx, txref, elem_R(el[rr0 - er.x]));
+        }
+    };
+    fill_table(0);
+
+    float Dr[kC][P], Wr[kC][P], Ar[kC][P], gR[kC];
+    float dr_min = 0.0f, dr_max = 0.0f, accC = 0.0f;
+    unsigned cmask = 0u;
+    RegStage<float, SYM> rs;
+    // Weight-gradient partials of the current chunk -> shared per-element sums.
+    auto flush_chunk = [&](int r0c) {
+        if (!NEED_PAR || cmask == 0u) return;
+#pragma unroll
+        for (int c = 0; c < kC; ++c) {
+            if (!((cmask >> c) & 1u)) continue;
+            const float v = warp_sum(gR[c]);
+            if (lane == 0 && v != 0.0f) atomicAdd(&ge[r0c + c - er.x], v);
+        }
+    };
+
+    int k = k_a, j = 0;
+    int k1 = k_a, j1 = 0;
+    __syncthreads();
+    if (n_stages > 0) {
+        advance(k1, j1);
+        const StageInfo s0 = st[0];
+        const int rr0 = er.x + k_a * kC;
+        if (!s0.skip()) stage_prefetch<float, SYM>(rs, a, rf, s0, tx_of(0), rr0, min(rr0 + kC - 1, er.y), vec_ok);
+    }
+    for (int q = 0; q < n_stages; ++q) {
+        const int r0 = er.x + k * kC;
+        const int r_last = min(r0 + kC - 1, er.y);
+        const int t = tx_of(j);
+        const StageInfo si = st[q & (kTableStages - 1)];
+        if (!si.skip()) stage_store<float, SYM>(rs, buf, a, si, t, r0, r_last);
+        __syncthreads();   // pairs of stage q visible; cotangent window zero
+        if (q + 1 < n_stages) {
+            if (((q + 1) & (kTableBatch - 1)) == 0) {
+                fill_table(q + 1);
+                __syncthreads();
+            }
+            const StageInfo s1 = st[(q + 1) & (kTableStages - 1)];
+            const int rr0 = er.x + k1 * kC;
+            if (!s1.skip()) stage_prefetch<float, SYM>(rs, a, rf, s1, tx_of(j1), rr0, min(rr0 + kC - 1, er.y), vec_ok);
+        }
+        if (j == 0) {
+            if (q > 0) flush_chunk(r0 - kC);
+            cmask = 0u;
+#pragma unroll
+            for (int c = 0; c < kC; ++c) {
+                gR[c] = 0.0f;
+                if (r0 + c <= r_last && r0 + c >= wr.x && r0 + c <= wr.y) cmask |= 1u << c;
+            }
+            if (cmask) {
+                const Elem e0 = el[r0 - er.x];
+                float mn = 3.0e38f, mx = -3.0e38f;
+#pragma unroll
+                for (int c = 0; c < kC; ++c) {
+                    const bool on = (cmask >> c) & 1u;
+                    const Elem ee = el[(on ? r0 + c : r0) - er.x];
+                    const float cc = elem_rel(ee, e0);
+#pragma unroll
+                    for (int p = 0; p < P; ++p) {
+                        Dr[c][p] = on ? cc + dist_delta(ee, ux, kz[p]) : 0.0f;
+                        Ar[c][p] = on ? apod_w(g.apod, -(ee.ax + ux), kap[p]) : 0.0f;
+                        Wr[c][p] = Ar[c][p] * ee.g;
+                        if (on) {
+                            mn = fminf(mn, Dr[c][p]);
+                            mx = fmaxf(mx, Dr[c][p]);
+                        }
+                    }
+                }
+                dr_min = warp_min(mn);
+                dr_max = warp_max(mx);
+            }
+        }
+        unsigned cm = cmask;
+        if (SYM && t > r0) cm &= ~((1u << (t - r0)) - 1u);
+        bool live = !si.skip() && cm != 0u;
+        if (MODE == 0) live = live && a.tx[t].e >= wr.x && a.tx[t].e <= wr.y;
+        float tw[P], yt[P], ya[P];
+        if (live) {
+            if (MODE == 0) {
+                const Elem et = el[a.tx[t].e - er.x];
+                float mn = 3.0e38f, mx = -3.0e38f;
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    tw[p] = si.B + dist_delta(et, ux, kz[p]);
+                    const float at = apod_w(g.apod, -(et.ax + ux), kap[p]);
+                    ya[p] = y[p] * at;          // y a_t: transmit-weight gradient
+                    yt[p] = ya[p] * et.g;       // y w_t
+                    mn = fminf(mn, tw[p]);
+                    mx = fmaxf(mx, tw[p]);
+                }
+                if (si.edge()) {
+                    mn = warp_min(mn);
+                    mx = warp_max(mx);
+                    live = ((float)si.lo + mn + dr_min <= (float)(a.ns - 1) + 0.5f) &&
+                           ((float)si.lo + mx + dr_max >= -0.5f);
+                }
+            } else {
+                const float sn = a.tx[t].sin_f, cs = a.tx[t].cos_f;
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    tw[p] = si.B + fmaf(ux, sn, uz[p] * cs);
+                    yt[p] = y[p];
+                    ya[p] = 0.0f;
+                }
+            }
+        }
+        if (live) {
+            const TxInfo& ti = a.tx[t];
+            const float base_c = (float)si.lo + (ti.t0.hi + ti.t0.lo);   // s + base_c = path in samples
+            float gT = 0.0f;
+#pragma unroll
+            for (int c = 0; c < kC; ++c) {
+                if (!((cm >> c) & 1u)) continue;
+                const float2* bc = buf + c * a.W;
+                float* gc = gw + c * GW;
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    const float s = tw[p] + Dr[c][p];
+                    const float m = __fadd_rd(s, kMagic);
+                    const float f = s - (m - kMagic);
+                    const int idx = __float_as_int(m) - kMagicBits;
+                    const float2 ab = bc[idx];
+                    const float v = fmaf(f, ab.y, ab.x);
+                    const bool ok = (unsigned)(si.lo + idx) <= (unsigned)(a.ns - 2);
+                    const float yW = ok ? yt[p] * Wr[c][p] : 0.0f;
+                    if (NEED_RF && yW != 0.0f) {
+                        atomicAdd(gc + idx, yW - yW * f);
+                        atomicAdd(gc + idx + 1, yW * f);
+                    }
+                    if (NEED_PAR) {
+                        accC = fmaf(yW * ab.y, base_c + s, accC);
+                        gR[c] = fmaf(yt[p] * Ar[c][p], v, gR[c]);
+                        if (MODE == 0) gT = fmaf(ya[p] * Wr[c][p], v, gT);
+                    }
+                }
+            }
+            if (NEED_PAR && MODE == 0) {
+                gT = warp_sum(gT);
+                if (lane == 0 && gT != 0.0f) atomicAdd(&ge[a.tx[t].e - er.x], gT);
+            }
+        }
+        if (NEED_RF) {
+            __syncthreads();   // every contribution of stage q is in the window; pairs no longer read
+            if (!si.skip()) {
+                // window position n covers samples lo + n, n in [0, len]; rows paired with t
+                const int span = si.len + 1, nrow = r_last - r0 + 1;
+                for (int i = tid; i < nrow * span; i += kThreads) {
+                    const int c = i / span, n = i - c * span;
+                    float* cell = gw + c * GW + n;
+                    const float v = *cell;
+                    if (v == 0.0f) continue;
+                    *cell = 0.0f;
+                    const int smp = si.lo + n;
+                    if (smp < 0 || smp >= a.ns) continue;
+                    atomicAdd(grf + ((long long)t * E + r0 + c) * a.ns + smp, v);
+                    if (SYM && r0 + c > t) atomicAdd(grf + ((long long)(r0 + c) * E + t) * a.ns + smp, v);
+                }
+            }
+        } else {
+            __syncthreads();   // pairs no longer read
+        }
+        k = k1;
+        j = j1;
+        advance(k1, j1);
+    }
+    if (NEED_PAR) {
+        if (n_stages > 0) flush_chunk(er.x + (k_b - 1) * kC);   // the CTA's last chunk
+        const float sc = warp_sum(accC);
+        if (lane == 0) s_red[warp] = sc;
+        __syncthreads();
+        if (tid == 0) {
+            float tot = 0.0f;
+            for (int w = 0; w < kThreads / 32; ++w) tot += s_red[w];
+            if (tot != 0.0f && a.grad_c) atomicAdd(a.grad_c, tot * a.neg_inv_c);
+        }
+        if (a.grad_w)
+            for (int e = er.x + tid; e <= er.y; e += kThreads) {
+                const float v = ge[e - er.x];
+                if (v != 0.0f) atomicAdd(a.grad_w + e, v);
+            }
+    }
+}
+
+// Per-pixel reverse mode for grids so coarse that a tile's staging window does
+// not fit in shared memory (the forward's direct path): delays in
+// double-float, every contribution straight to global memory with atomics.
+template <int MODE>
+__global__ void __launch_bounds__(256) das_backward_direct_kernel(const __grid_constant__ DasArgs a) {
+    const Geom& g = a.g;
+    const int ix = blockIdx.x * 32 + (threadIdx.x & 31);
+    const int iz = blockIdx.y * 8 + (threadIdx.x >> 5);
+    const int b = blockIdx.z;
+    float accC = 0.0f;
+    if (ix < g.nx && iz < g.nz) {
+        const float y = __ldg(a.grad_out + ((long long)b * g.nz + iz) * g.nx + ix);
+        const float* rf = reinterpret_cast<const float*>(a.rf) + (long long)b * a.frame_elems;
+        float* grf = a.grad_rf ? a.grad_rf + (long long)b * a.frame_elems : nullptr;
+        const DF px = df_axpk(a.gd.gx0, ix, a.gd.gdx), pz = df_axpk(a.gd.gz0, iz, a.gd.gdz);
+        const DF pz2 = df_mul(pz, pz);
+        const float kap = aperture_kappa(g, pz.hi);
+        const int2 er = tile_elements(g, px.hi, px.hi, pz.hi);
+        auto dist = [&](int e, float& dxe) {
+            const DF d = df_add(df_axpk(a.gd.xe0, e, a.gd.pitch), df_neg(px));
+            dxe = d.hi;
+            return df_sqrt(df_add(df_mul(d, d), pz2));
+        };
+        auto weight = [&](int e) { return g.elem_weight ? __ldg(g.elem_weight + e) : 1.0f; };
+        for (int t = 0; t < a.n_tx && y != 0.0f; ++t) {
+            const TxInfo& ti = a.tx[t];
+            DF dt;
+            float at = 1.0f, gt = 1.0f;
+            if (MODE == 0) {
+                float dxe;
+                dt = df_add(dist(ti.e, dxe), df_neg(ti.t0));
+                at = apod_w(g.apod, dxe, kap);
+                gt = weight(ti.e);
+            } else {
+                dt = df_add(df_add(df_mul(px, ti.sin), df_mul(pz, ti.cos)), df_neg(ti.t0));
+            }
+            if (at == 0.0f) continue;
+            const float t0 = ti.t0.hi + ti.t0.lo;
+            float gT = 0.0f;
+            for (int r = er.x; r <= er.y; ++r) {
+                float dxe;
+                const DF dr = dist(r, dxe);
+                const float ar = apod_w(g.apod, dxe, kap);
+                if (ar == 0.0f) continue;
+                const DF sd = df_add(dt, dr);
+                float fl = floorf(sd.hi);
+                float f = (sd.hi - fl) + sd.lo;
+                if (f < 0.0f) { fl -= 1.0f; f += 1.0f; }
+                if (f >= 1.0f) { fl += 1.0f; f -= 1.0f; }
+                if (!(fl >= 0.0f) || !(fl <= (float)(a.ns - 2))) continue;
+                const long long off = ((long long)t * g.n_elements + r) * a.ns + (int)fl;
+                const float x0 = __ldg(rf + off), x1 = __ldg(rf + off + 1);
+                const float v = fmaf(f, x1 - x0, x0);
+                const float gr = weight(r);
+                const float yW = y * (gt * at) * (gr * ar);
+                if (grf) {
+                    atomicAdd(grf + off, yW - yW * f);
+                    atomicAdd(grf + off + 1, yW * f);
+                }
+                accC = fmaf(yW * (x1 - x0), (fl + f) + t0, accC);
+                if (a.grad_w) {
+                    atomicAdd(a.grad_w + r, y * (gt * at) * ar * v);
+                    if (MODE == 0) gT = fmaf(y * at * (gr * ar), v, gT);
+                }
+            }
+            if (MODE == 0 && a.grad_w && gT != 0.0f) atomicAdd(a.grad_w + ti.e, gT);
+        }
+    }
+    accC = warp_sum(accC);
+    if ((threadIdx.x & 31) == 0 && accC != 0.0f && a.grad_c) atomicAdd(a.grad_c, accC * a.neg_inv_c);
+}
+
+template <int MODE, bool SYM, bool NEED_RF, bool NEED_PAR>
+wf_status launch_bwd_v(DasArgs& A, const Plan& P, int batch, cudaStream_t st) {
+    static unsigned long long smem_set = 0ull;
+    auto kern = das_backward_kernel<MODE, SYM, NEED_RF, NEED_PAR>;
+    wf_status s = ensure_smem_limit(kern, kMaxTiledSmem, smem_set);
+    if (s != WF_OK) return s;
+    const size_t smem = bwd_smem_layout(A.W, A.g.n_elements, NEED_RF).total;
+    kern<<<dim3(P.n_items, batch), kThreads, smem, st>>>(A);
+    return last_launch_status();
+}
+
+template <int MODE, bool SYM>
+wf_status launch_bwd_need(DasArgs& A, const Plan& P, int batch, bool need_rf, bool need_par,
+                          cudaStream_t st) {
+    if (need_rf && need_par) return launch_bwd_v<MODE, SYM, true, true>(A, P, batch, st);
+    if (need_rf) return launch_bwd_v<MODE, SYM, true, false>(A, P, batch, st);
+    return launch_bwd_v<MODE, SYM, false, true>(A, P, batch, st);
+}
+
+template <int MODE>
+wf_status launch_das_backward(DasArgs& A, const Plan& P, int batch, bool need_rf, bool need_par,
+                              cudaStream_t st) {
+    if (P.cfg.wcol != kBwdWCOL || P.cfg.p != kBwdP) return WF_ERR_UNSUPPORTED;
+    if (!need_rf && !need_par) return WF_OK;
+    if (!P.tiled || bwd_smem_layout(A.W, A.g.n_elements, need_rf).total > kMaxTiledSmem) {
+        dim3 grid((A.g.nx + 31) / 32, (A.g.nz + 7) / 8, batch);
+        das_backward_direct_kernel<MODE><<<grid, 256, 0, st>>>(A);
+        return last_launch_status();
+    }
+    if (MODE == 0 && P.sym) return launch_bwd_need<MODE, MODE == 0>(A, P, batch, need_rf, need_par, st);
+    return launch_bwd_need<MODE, false>(A, P, batch, need_rf, need_par, st);
+}
+
+template wf_status launch_das_backward<0>(DasArgs&, const Plan&, int, bool, bool, cudaStream_t);
+template wf_status launch_das_backward<1>(DasArgs&, const Plan&, int, bool, bool, cudaStream_t);
+
+}  // namespace wf

@@ -1,0 +1,1025 @@
+// Delay-and-sum beamforming kernels for STAI and PWI (paper Sec. II-B, Fig. 2 "Beamforming").
+//
+// b(p) = sum_t Wt(p,t) sum_r Wr(p,r) lerp(rf[t][r], Dt(p,t) + Dr(p,r))
+//   STAI: Dt = |p - x_{e_t}| - t_start fs,   Wt = apod(p, e_t) g_{e_t}
+//   PWI:  Dt = x sin th + z cos th - t0 fs,   Wt = 1
+//   both: Dr = |p - x_r|,                     Wr = apod(p, r) g_r
+// (all lengths in samples).  DAS is a gather-sum, not a contraction: no
+// tensor cores.  Design (GB300):
+//  * a CTA (8 warps) owns a pixel tile and one group of receive chunks, and
+//    loops over every transmit for them, chunk-outer.  A warp covers WCOL
+//    columns; its lanes (and P pixels per lane) run down the rows (tile 32 x 32
+//    for P = 4).  Receive distances and weights of a chunk of 8 elements are
+//    computed once per tile in registers and reused by every transmit; the
+//    transmit term of a stage is recomputed per pixel (one distance and one
+//    weight for STAI, one FMA for PWI).  Tiles are launched deepest row first:
+//    the deep tiles have the widest apertures and carry most of the work.
+//  * reciprocity (STAI with every element firing once, in element order): the
+//    pairs (t, r) and (r, t) have the same delay and weights, so only t <= r is
+//    evaluated, on the staged sum rf[t][r] + rf[r][t] (rf[t][t] alone on the
+//    diagonal).  Linear interpolation is linear in the samples, so this is the
+//    same sum with half the gathers.
+//  * geometry is tile-relative: the tile origin c is the reference point and
+//    R_e = |c - x_e| is formed in double-float arithmetic (two FP32 words); a
+//    pixel at c + u needs only the small FP32 correction
+//      delta = |c + u - x_e| - R_e = N / (R_e + |c + u - x_e|),
+//      N = u_x (2 (c_x - x_e) + u_x) + u_z (2 c_z + u_z),
+//    and every fractional delay is formed relative to its staging window, so
+//    FP32 carries a few hundred samples of range instead of thousands;
+//  * for every (transmit, receive chunk) the sample window the tile can touch
+//    (exact convex bounds of the delay over the tile) is copied by TMA bulk
+//    copies into a shared-memory ring and converted to FP32 pairs
+//    (x[i], x[i+1]-x[i]): one 8-byte shared load and one FMA interpolate a
+//    sample.  The int16 scale is folded into the receive weights;
+//  * warps skip stages whose transmit or receive chunk lies outside their
+//    aperture or whose delays all fall outside the record;
+//  * the floor of the window-relative delay is a round-down add of 1.5 * 2^23;
+//  * partial images of the chunk groups go to the workspace and a second
+//    kernel sums them in group order (deterministic).
+#pragma once
+
+#include <cuda_fp16.h>
+
+#include "common.cuh"
+
+namespace wf {
+
+constexpr int kThreads = 256;              // 8 warps
+constexpr int kC = 8;                      // receive elements per chunk
+constexpr int kMaxWindow = 512;            // staged positions per trace: 64 segments of 8
+constexpr int kMaxGroups = 8;              // receive-chunk groups per tile
+constexpr float kMagic = 12582912.0f;      // 1.5 * 2^23
+constexpr int kMagicBits = 0x4B400000;
+
+struct TxInfo {
+    DF sin, cos, t0;   // PWI steering (double-float); both: t0 = time of sample 0 times fs
+    float sin_f, cos_f;
+    int e;             // STAI: element fired
+    int pad;
+};
+
+// Sample-unit geometry as double-floats (reference terms) next to the float copy in Geom.
+struct GeomDF {
+    DF gx0, gdx, gz0, gdz, xe0, pitch;
+};
+
+struct DasArgs {
+    Geom g;
+    GeomDF gd;
+    int n_tx, ns;
+    int tiles_x, tiles_z;
+    int n_groups, n_items;           // items per frame = tiles * groups
+    int W;                           // staged positions per trace (shared stride)
+    int ring;                        // TMA raw-sample ring depth
+    int sym;                         // delay probe: reciprocal STAI pairing in use
+    const void* rf;
+    float rf_scale;
+    long long frame_elems;           // n_tx * E * ns
+    float* part;                     // [batch][n_items][256 * P] group partials
+    float* out;
+    WsHeader* hdr;
+    // reverse mode (wf_das_backward) only
+    const float* grad_out;           // [batch][nz][nx] cotangent of the image
+    float* grad_rf;                  // [batch][n_tx][E][ns] or null
+    float* grad_w;                   // [E] or null
+    float* grad_c;                   // [1] or null
+    float neg_inv_c;                 // -1 / c (s per m/s of sound speed)
+    TxInfo tx[WF_MAX_TX];
+};
+
+// Tile shape of a kernel configuration.
+template <int WCOL, int P>
+struct Shape {
+    static constexpr int kLR = 32 / WCOL;     // lane rows per warp
+    static constexpr int kCols = 8 * WCOL;    // tile columns
+    static constexpr int kRows = kLR * P;     // tile rows
+};
+
+// Apodization weight given the lateral offset xe - x and kap = 2F / z.
+// Hann 0.5 (1 + cos(pi u)) is evaluated as cos^2(pi u / 2) with the fast
+// cosine (absolute error < 4e-7 on |pi u / 2| < pi / 2).
+__device__ __forceinline__ float apod_w(int apod, float dxe, float kap) {
+    if (apod == WF_APOD_NONE) return 1.0f;
+    const float u = dxe * kap;
+    if (!(kap > 0.0f) || !(fabsf(u) < 1.0f)) return 0.0f;
+    if (apod == WF_APOD_RECT) return 1.0f;
+    const float c = __cosf(u * 1.5707963267948966f);
+    return c * c;
+}
+
+// Per-element reference data of a tile (shared memory): R_e = Rhi + Rlo,
+// c_x - x_e and the element weight.
+struct Elem {
+    float Rhi, Rlo, ax, g;
+};
+
+__device__ __forceinline__ DF elem_R(const Elem& e) { return DF{e.Rhi, e.Rlo}; }
+
+// Distance from the reference point (cx, cz) to element e, in double-float
+// (relative error ~1e-13, far below the FP32 corrections added to it).
+__device__ __forceinline__ Elem make_elem(const DasArgs& a, DF cx, DF cz, int e) {
+    const DF xe = df_axpk(a.gd.xe0, e, a.gd.pitch);
+    const DF ax = df_add(cx, df_neg(xe));
+    const DF R = df_sqrt(df_add(df_mul(ax, ax), df_mul(cz, cz)));
+    Elem el;
+    el.Rhi = R.hi;
+    el.Rlo = R.lo;
+    el.ax = ax.hi;
+    el.g = a.g.elem_weight ? __ldg(a.g.elem_weight + e) : 1.0f;
+    return el;
+}
+
+// FP32 correction |c + u - x_e| - R_e for a pixel at offset (ux, uz); kz = uz (2 cz + uz).
+__device__ __forceinline__ float dist_delta(const Elem& el, float ux, float kz) {
+    const float n = fmaf(ux, 2.0f * el.ax + ux, kz);
+    const float t = fmaf(el.Rhi, el.Rhi, n);
+    const float d = t > 0.0f ? t * rsqrtf(t) : 0.0f;
+    const float den = el.Rhi + d;
+    return den > 0.0f ? __fdividef(n, den) : 0.0f;
+}
+
+// R_e - R_ref of two elements of the same tile, in FP32 (the hi parts differ exactly).
+__device__ __forceinline__ float elem_rel(const Elem& e, const Elem& ref) {
+    return (e.Rhi - ref.Rhi) + (e.Rlo - ref.Rlo);
+}
+
+// Element range that can be inside the aperture of some pixel of [xlo, xhi] x [.., zhi].
+__device__ __forceinline__ int2 tile_elements(const Geom& g, float xlo, float xhi, float zhi) {
+    if (g.apod == WF_APOD_NONE) return make_int2(0, g.n_elements - 1);
+    if (!(zhi > 0.0f)) return make_int2(1, 0);
+    const float half = zhi / g.two_f;
+    const int lo = (int)floorf((xlo - half - g.xe0) / g.pitch) - 1;
+    const int hi = (int)ceilf((xhi + half - g.xe0) / g.pitch) + 1;
+    return make_int2(max(lo, 0), min(hi, g.n_elements - 1));
+}
+
+// Exact range over the rectangle [xlo, xhi] x [zlo, zhi] of the delay of one
+// (transmit, receive element) pair, FP32.  Both delay forms are convex in x
+// and increase with z >= 0, so the maximum sits on a bottom corner and the
+// minimum on the top edge at the clamped stationary point: the midpoint of
+// the two elements for STAI, x_r - z tan(th) for PWI.
+template <int MODE>
+__device__ __forceinline__ float2 pair_bounds(const Geom& g, const TxInfo& ti, int r, float xlo,
+                                              float xhi, float zlo, float zhi) {
+    const float xr = elem_x(g, r);
+    const float c = -ti.t0.hi;
+    if (MODE == 0) {
+        const float xt = elem_x(g, ti.e);
+        const float xm = fminf(fmaxf(0.5f * (xt + xr), xlo), xhi);
+        const float a0 = xm - xt, b0 = xm - xr;
+        const float mn = sqrtf(fmaf(a0, a0, zlo * zlo)) + sqrtf(fmaf(b0, b0, zlo * zlo));
+        const float a1 = xlo - xt, b1 = xlo - xr, a2 = xhi - xt, b2 = xhi - xr;
+        const float z2 = zhi * zhi;
+        const float mx = fmaxf(sqrtf(fmaf(a1, a1, z2)) + sqrtf(fmaf(b1, b1, z2)),
+                               sqrtf(fmaf(a2, a2, z2)) + sqrtf(fmaf(b2, b2, z2)));
+        return make_float2(mn + c, mx + c);
+    }
+    const float xm = fminf(fmaxf(xr - zlo * (ti.sin_f / ti.cos_f), xlo), xhi);
+    const float b0 = xm - xr;
+    const float mn = fmaf(xm, ti.sin_f, zlo * ti.cos_f) + sqrtf(fmaf(b0, b0, zlo * zlo));
+    const float b1 = xlo - xr, b2 = xhi - xr, z2 = zhi * zhi;
+    const float mx = fmaxf(fmaf(xlo, ti.sin_f, zhi * ti.cos_f) + sqrtf(fmaf(b1, b1, z2)),
+                           fmaf(xhi, ti.sin_f, zhi * ti.cos_f) + sqrtf(fmaf(b2, b2, z2)));
+    return make_float2(mn + c, mx + c);
+}
+
+// Transmit reference term at the reference point (double-float).
+template <int MODE>
+__device__ __forceinline__ DF tx_ref(const TxInfo& ti, DF cx, DF cz, DF R_et) {
+    if (MODE == 0) return df_add(R_et, df_neg(ti.t0));
+    return df_add(df_add(df_mul(cx, ti.sin), df_mul(cz, ti.cos)), df_neg(ti.t0));
+}
+
+__device__ __forceinline__ void flag(WsHeader* h, unsigned bit, unsigned a, unsigned b, unsigned c) {
+    if (atomicOr(&h->flags, bit) == 0u) {
+        h->first_bad[0] = a;
+        h->first_bad[1] = b;
+        h->first_bad[2] = c;
+    }
+}
+
+// Tile geometry shared by the DAS kernel and the delay probe; the origin pixel
+// of the tile is the reference point.
+struct TileGeo {
+    int ix0, iz0;
+    DF cx, cz;
+    float xlo, xhi, zlo, zhi;
+    int2 er;
+};
+
+template <int COLS, int ROWS>
+__device__ __forceinline__ TileGeo tile_geo(const DasArgs& a, int ix0, int iz0) {
+    const Geom& g = a.g;
+    TileGeo t;
+    t.ix0 = ix0;
+    t.iz0 = iz0;
+    t.cx = df_axpk(a.gd.gx0, ix0, a.gd.gdx);
+    t.cz = df_axpk(a.gd.gz0, iz0, a.gd.gdz);
+    t.xlo = pixel_x(g, ix0);
+    t.xhi = pixel_x(g, ix0 + COLS - 1);
+    t.zlo = pixel_z(g, iz0);
+    t.zhi = pixel_z(g, iz0 + ROWS - 1);
+    t.er = tile_elements(g, t.xlo, t.xhi, t.zhi);
+    return t;
+}
+
+// Launch rank of a tile: deepest tile row first.
+__host__ __device__ inline int tile_rank(int tz, int tx, int tiles_z, int tiles_x) {
+    return (tiles_z - 1 - tz) * tiles_x + tx;
+}
+
+// Staging window of one (transmit, receive chunk) stage: the first staged
+// sample lo (multiple of 8), the staged length (multiple of 8, <= W), the FP32
+// window-relative base B = tx_ref + R_{r0} - lo, and flags (bit 0: no sample of
+// the window is inside the record; bit 1: the window crosses an end of the
+// record; bits 2..: clamped over-long window length).
+struct StageInfo {
+    int lo, len;
+    float B;
+    int flags;
+    __device__ __forceinline__ bool skip() const { return flags & 1; }
+    __device__ __forceinline__ bool edge() const { return (flags >> 1) & 1; }
+    __device__ __forceinline__ int over() const { return flags >> 2; }
+};
+
+__device__ __forceinline__ StageInfo make_stage(const DasArgs& a, float mn, float mx, DF txref,
+                                                DF R_r0) {
+    StageInfo si;
+    si.lo = ((int)floorf(mn) - 2) & ~7;
+    si.len = (((int)ceilf(mx) + 2 - si.lo + 1) + 7) & ~7;
+    const int skip = (si.lo + si.len <= 0 || si.lo > a.ns - 2) ? 1 : 0;
+    const DF x = df_add(txref, R_r0);
+    si.B = (x.hi - (float)si.lo) + x.lo;   // x.hi - lo is exact: lo is an integer near x.hi
+    const int over = si.len > a.W ? si.len : 0;
+    if (over) si.len = a.W;
+    const int edge = (si.lo >= 0 && si.lo + si.len <= a.ns - 1) ? 0 : 1;
+    si.flags = skip | (edge << 1) | (over << 2);
+    return si;
+}
+
+// Reciprocal STAI stage bookkeeping.  With n_e elements in the tile's range
+// and nc = ceil(n_e / 8) receive chunks, chunk k pairs with the transmits
+// er.x .. er.x + min(8 (k + 1), n_e) - 1 (those not after its last element).
+// Stages before chunk k:
+__host__ __device__ inline int sym_prefix(int k, int nc, int n_e) {
+    return k < nc ? 4 * k * (k + 1) : 4 * (nc - 1) * nc + n_e;
+}
+// Chunk of the stage with global index qg (0 <= qg < sym_prefix(nc, nc, n_e)).
+__device__ __forceinline__ int sym_chunk(int qg, int nc) {
+    int k = (int)((sqrtf(1.0f + (float)qg) - 1.0f) * 0.5f);
+    k = max(0, min(k, nc - 1));
+    while (k < nc - 1 && 4 * (k + 1) * (k + 2) <= qg) ++k;
+    while (k > 0 && 4 * k * (k + 1) > qg) --k;
+    return k;
+}
+
+// ---------------------------------------------------------------------------
+// TMA staging: bulk asynchronous copies (cp.async.bulk) of raw trace windows
+// into a shared-memory ring, completion tracked by mbarriers.  Every wait is
+// bounded: on timeout the kernel records a flag in the workspace header and
+// carries on (its result is then unspecified, the call reports WF_ERR_INTERNAL
+// through wf_workspace_check) instead of spinning forever.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0u;
+}
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes,
+                                              unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void fence_async_shared() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+constexpr unsigned kWaitLimit = 1u << 22;   // try_wait rounds before a wait is declared stuck
+
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity) {
+    for (unsigned i = 0; i < kWaitLimit; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (i >= 16) __nanosleep(64);
+    }
+    return false;
+}
+
+// Raw samples of one staging segment (8 consecutive samples + the next one)
+// held in registers between the load and the conversion.
+template <typename T> struct Seg;
+template <> struct Seg<int16_t> {
+    uint4 v;
+    int nxt;
+    __device__ __forceinline__ float at(int k) const {
+        const unsigned w = (k >> 1) == 0 ? v.x : (k >> 1) == 1 ? v.y : (k >> 1) == 2 ? v.z : v.w;
+        return (float)((k & 1) ? ((int)w >> 16) : (int)(short)(w & 0xffffu));
+    }
+};
+template <> struct Seg<__half> {
+    uint4 v;
+    int nxt;
+    __device__ __forceinline__ float at(int k) const {
+        const unsigned w = (k >> 1) == 0 ? v.x : (k >> 1) == 1 ? v.y : (k >> 1) == 2 ? v.z : v.w;
+        return __half2float(__ushort_as_half((unsigned short)((k & 1) ? (w >> 16) : (w & 0xffffu))));
+    }
+};
+template <> struct Seg<float> {
+    float4 v0, v1;
+    int nxt;
+    __device__ __forceinline__ float at(int k) const {
+        switch (k) {
+            case 0: return v0.x; case 1: return v0.y; case 2: return v0.z; case 3: return v0.w;
+            case 4: return v1.x; case 5: return v1.y; case 6: return v1.z; default: return v1.w;
+        }
+    }
+};
+
+template <typename T> __device__ __forceinline__ float raw_one(int bits);
+template <> __device__ __forceinline__ float raw_one<int16_t>(int bits) { return (float)(short)bits; }
+template <> __device__ __forceinline__ float raw_one<__half>(int bits) {
+    return __half2float(__ushort_as_half((unsigned short)bits));
+}
+template <> __device__ __forceinline__ float raw_one<float>(int bits) { return __int_as_float(bits); }
+
+template <typename T> __device__ __forceinline__ int raw_bits(const T* p);
+template <> __device__ __forceinline__ int raw_bits<int16_t>(const int16_t* p) {
+    return (int)(unsigned short)__ldg(p);
+}
+template <> __device__ __forceinline__ int raw_bits<__half>(const __half* p) {
+    return (int)__ldg(reinterpret_cast<const unsigned short*>(p));
+}
+template <> __device__ __forceinline__ int raw_bits<float>(const float* p) { return __float_as_int(__ldg(p)); }
+
+// Load samples [n0, n0 + 8) of a trace and sample n0 + 8 (zero outside [0, ns)).
+template <typename T>
+__device__ __forceinline__ void seg_load(Seg<T>& sg, const T* tr, int n0, int ns, bool vec_ok) {
+    if (vec_ok && n0 >= 0 && n0 + 8 <= ns) {
+        if constexpr (sizeof(T) == 2) {
+            sg.v = __ldg(reinterpret_cast<const uint4*>(tr + n0));
+        } else {
+            sg.v0 = __ldg(reinterpret_cast<const float4*>(tr + n0));
+            sg.v1 = __ldg(reinterpret_cast<const float4*>(tr + n0 + 4));
+        }
+    } else {
+        int b[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) b[k] = (n0 + k >= 0 && n0 + k < ns) ? raw_bits<T>(tr + n0 + k) : 0;
+        if constexpr (sizeof(T) == 2) {
+            sg.v = make_uint4((unsigned)(b[0] & 0xffff) | ((unsigned)b[1] << 16),
+                              (unsigned)(b[2] & 0xffff) | ((unsigned)b[3] << 16),
+                              (unsigned)(b[4] & 0xffff) | ((unsigned)b[5] << 16),
+                              (unsigned)(b[6] & 0xffff) | ((unsigned)b[7] << 16));
+        } else {
+            sg.v0 = make_float4(__int_as_float(b[0]), __int_as_float(b[1]), __int_as_float(b[2]),
+                                __int_as_float(b[3]));
+            sg.v1 = make_float4(__int_as_float(b[4]), __int_as_float(b[5]), __int_as_float(b[6]),
+                                __int_as_float(b[7]));
+        }
+    }
+    sg.nxt = (n0 + 8 >= 0 && n0 + 8 < ns) ? raw_bits<T>(tr + n0 + 8) : 0;
+}
+
+// Load samples [8k, 8k + 9) of a raw shared-memory row (16-byte aligned).
+template <typename T>
+__device__ __forceinline__ void seg_load_smem(Seg<T>& sg, const T* row, int k) {
+    if constexpr (sizeof(T) == 2) {
+        sg.v = *reinterpret_cast<const uint4*>(row + 8 * k);
+        sg.nxt = (int)*reinterpret_cast<const unsigned short*>(row + 8 * k + 8);
+    } else {
+        sg.v0 = *reinterpret_cast<const float4*>(row + 8 * k);
+        sg.v1 = *reinterpret_cast<const float4*>(row + 8 * k + 4);
+        sg.nxt = __float_as_int(row[8 * k + 8]);
+    }
+}
+
+// Store 8 FP32 pairs (x[n], x[n+1] - x[n]) for n = n0 .. n0 + 7 from 9
+// consecutive samples; pairs whose n is outside [0, ns - 2] are zero (no
+// recorded neighbour).
+__device__ __forceinline__ void pairs_store(const float (&v)[9], float2* dst, int n0, int ns) {
+    const bool full = n0 >= 0 && n0 + 9 <= ns;
+    float4* d4 = reinterpret_cast<float4*>(dst);
+#pragma unroll
+    for (int k = 0; k < 8; k += 2) {
+        float2 p0 = make_float2(v[k], v[k + 1] - v[k]);
+        float2 p1 = make_float2(v[k + 1], v[k + 2] - v[k + 1]);
+        if (!full) {
+            if (!(n0 + k >= 0 && n0 + k <= ns - 2)) p0 = make_float2(0.0f, 0.0f);
+            if (!(n0 + k + 1 >= 0 && n0 + k + 1 <= ns - 2)) p1 = make_float2(0.0f, 0.0f);
+        }
+        d4[k >> 1] = make_float4(p0.x, p0.y, p1.x, p1.y);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void seg_store(const Seg<T>& sg, float2* dst, int n0, int ns) {
+    float v[9];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = sg.at(k);
+    v[8] = raw_one<T>(sg.nxt);
+    pairs_store(v, dst, n0, ns);
+}
+
+// Pairs of the sum of two traces (reciprocal STAI: rf[t][r] + rf[r][t]).
+template <typename T>
+__device__ __forceinline__ void seg_store_sum(const Seg<T>& sa, const Seg<T>& sb, float2* dst, int n0,
+                                              int ns) {
+    float v[9];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = sa.at(k) + sb.at(k);
+    v[8] = raw_one<T>(sa.nxt) + raw_one<T>(sb.nxt);
+    pairs_store(v, dst, n0, ns);
+}
+
+__device__ __forceinline__ void zero_segment(float2* dst) {
+    float4* d4 = reinterpret_cast<float4*>(dst);
+    const float4 z = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    d4[0] = z; d4[1] = z; d4[2] = z; d4[3] = z;
+}
+
+__device__ __forceinline__ float warp_min(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+constexpr int kTableStages = 256;  // stage-window ring in shared memory
+constexpr int kTableBatch = 128;   // windows computed per refill (one per thread)
+constexpr int kMaxRing = 3;        // TMA raw-sample ring depth
+
+// Shared-memory layout of the tiled kernel (byte offsets, all 16-byte aligned).
+struct SmemLayout {
+    size_t pairs, table, elems, raw, total;
+};
+
+__host__ __device__ inline SmemLayout smem_layout(int W, int n_elements, bool db, bool tma, bool sym,
+                                                  int ring, int rf_bytes) {
+    SmemLayout L;
+    size_t off = 0;
+    L.pairs = off;
+    off += (size_t)(db ? 2 : 1) * kC * W * sizeof(float2);
+    L.table = off;
+    off += (size_t)kTableStages * sizeof(StageInfo);
+    L.elems = off;
+    off += (((size_t)n_elements * sizeof(Elem)) + 15) & ~(size_t)15;
+    L.raw = off;
+    off += tma ? (size_t)ring * (sym ? 2 : 1) * kC * (W + 8) * rf_bytes : 0;
+    L.total = off;
+    return L;
+}
+
+// Segment (trace row c, block k) = (tid >> 6 [+ 4], tid & 63) of a stage, register path:
+// samples of trace rows A (rf[t][r0 + c]) and, reciprocal, B (rf[r0 + c][t]).
+template <typename T, bool SYM>
+struct RegStage {
+    Seg<T> a[2], b[2];
+};
+
+template <typename T, bool SYM>
+__device__ __forceinline__ void stage_prefetch(RegStage<T, SYM>& rs, const DasArgs& a, const T* rf,
+                                               const StageInfo& si, int t, int r0, int r_last,
+                                               bool vec_ok) {
+    const int nseg = si.len >> 3;
+    const int k = threadIdx.x & 63;
+    const long long E = a.g.n_elements;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int c = (threadIdx.x >> 6) + 4 * i;
+        if (k >= nseg || r0 + c > r_last) continue;
+        if (SYM && r0 + c < t) continue;
+        seg_load<T>(rs.a[i], rf + ((long long)t * E + r0 + c) * a.ns, si.lo + 8 * k, a.ns, vec_ok);
+        if (SYM && r0 + c > t)
+            seg_load<T>(rs.b[i], rf + ((long long)(r0 + c) * E + t) * a.ns, si.lo + 8 * k, a.ns, vec_ok);
+    }
+}
+
+template <typename T, bool SYM>
+__device__ __forceinline__ void stage_store(const RegStage<T, SYM>& rs, float2* buf, const DasArgs& a,
+                                            const StageInfo& si, int t, int r0, int r_last) {
+    const int nseg = si.len >> 3;
+    const int k = threadIdx.x & 63;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int c = (threadIdx.x >> 6) + 4 * i;
+        if (k >= nseg) continue;
+        float2* dst = buf + c * a.W + 8 * k;
+        const bool on = r0 + c <= r_last && (!SYM || r0 + c >= t);
+        if (!on) zero_segment(dst);
+        else if (SYM && r0 + c > t) seg_store_sum<T>(rs.a[i], rs.b[i], dst, si.lo + 8 * k, a.ns);
+        else seg_store<T>(rs.a[i], dst, si.lo + 8 * k, a.ns);
+    }
+}
+
+template <int MODE, typename T, int WCOL, int P, bool DB, bool TMA, bool CHECK, bool SYM>
+__global__ void __launch_bounds__(kThreads, 2) das_tiled_kernel(const __grid_constant__ DasArgs a) {
+    static_assert(!SYM || MODE == 0, "reciprocal pairing is an STAI property");
+    using S = Shape<WCOL, P>;
+    constexpr int kRawRows = SYM ? 2 * kC : kC;   // raw trace rows per ring slot
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const SmemLayout L = smem_layout(a.W, a.g.n_elements, DB, TMA, SYM, a.ring, (int)sizeof(T));
+    float2* buf0 = reinterpret_cast<float2*>(smem_raw + L.pairs);   // [DB+1][kC][W] pairs
+    StageInfo* st = reinterpret_cast<StageInfo*>(smem_raw + L.table);
+    Elem* el = reinterpret_cast<Elem*>(smem_raw + L.elems);         // [E range]
+    T* raw = reinterpret_cast<T*>(smem_raw + L.raw);                // [ring][kRawRows][W + 8]
+    __shared__ __align__(8) unsigned long long s_bar[kMaxRing];
+    __shared__ int s_tlist[WF_MAX_TX];
+    __shared__ int s_info[4];
+
+    const Geom& g = a.g;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int lx = lane % WCOL, lz = lane / WCOL;
+    const int item = blockIdx.x, b = blockIdx.y;
+    const int group = item % a.n_groups, rank = item / a.n_groups;
+    const int tzi = a.tiles_z - 1 - rank / a.tiles_x, txi = rank % a.tiles_x;
+    const TileGeo tg = tile_geo<S::kCols, S::kRows>(a, txi * S::kCols, tzi * S::kRows);
+    const T* rf = reinterpret_cast<const T*>(a.rf) + (long long)b * a.frame_elems;
+    const bool vec_ok = (a.ns & 7) == 0;
+    const int RW = a.W + 8;           // raw row stride (samples)
+    const int ring = TMA ? a.ring : 1;
+
+    // Pixel offsets from the reference point: column WCOL warp + lx, rows lz + kLR p.
+    const int col = WCOL * warp + lx;
+    const float ux = (float)col * g.gdx;
+    float kz[P], kap[P], uz[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        uz[p] = (float)(lz + S::kLR * p) * g.gdz;
+        kz[p] = uz[p] * fmaf(2.0f, tg.cz.hi, uz[p]);
+        kap[p] = aperture_kappa(g, tg.cz.hi + uz[p]);
+    }
+    // Elements that can weigh on this warp's columns (all rows of the tile).
+    const int2 wr = tile_elements(g, pixel_x(g, tg.ix0 + WCOL * warp),
+                                  pixel_x(g, tg.ix0 + WCOL * warp + WCOL - 1), tg.zhi);
+
+    const int2 er = tg.er;
+    const int n_e = er.y >= er.x ? er.y - er.x + 1 : 0;
+    const int nc = (n_e + kC - 1) / kC;
+    for (int e = er.x + tid; e <= er.y; e += kThreads) el[e - er.x] = make_elem(a, tg.cx, tg.cz, e);
+    if (tid == 0) {
+        int n = 0;
+        if (!SYM && n_e > 0)
+            for (int t = 0; t < a.n_tx; ++t) {
+                if (MODE == 0 && (a.tx[t].e < er.x || a.tx[t].e > er.y)) continue;
+                s_tlist[n++] = t;
+            }
+        // This group's receive chunks [ka, kb): equal stage counts per group.
+        const int G = a.n_groups;
+        int ka, kb, q0 = 0;
+        if (SYM) {
+            const long long total = sym_prefix(nc, nc, n_e);
+            ka = 0;
+            while (ka < nc && (long long)sym_prefix(ka, nc, n_e) * G < (long long)group * total) ++ka;
+            kb = ka;
+            while (kb < nc && (long long)sym_prefix(kb, nc, n_e) * G < (long long)(group + 1) * total) ++kb;
+            q0 = sym_prefix(ka, nc, n_e);
+        } else {
+            ka = (group * nc) / G;
+            kb = ((group + 1) * nc) / G;
+        }
+        s_info[0] = n;
+        s_info[1] = ka;
+        s_info[2] = kb;
+        s_info[3] = q0;
+        if (TMA) {
+            for (int i = 0; i < ring; ++i) mbar_init(&s_bar[i], 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+    }
+    __syncthreads();
+    const int n_act = s_info[0], k_a = s_info[1], k_b = s_info[2], q0 = s_info[3];
+    const int n_stages = n_e == 0 ? 0 : SYM ? sym_prefix(k_b, nc, n_e) - q0 : (k_b - k_a) * n_act;
+
+    // Stage q -> (receive chunk k, transmit slot j); transmit index of slot j.
+    auto locate = [&](int q, int& k, int& j) {
+        if (SYM) {
+            const int qg = q0 + q;
+            k = sym_chunk(qg, nc);
+            j = qg - 4 * k * (k + 1);
+        } else {
+            k = k_a + q / n_act;
+            j = q - (q / n_act) * n_act;
+        }
+    };
+    auto tx_of = [&](int j) { return SYM ? er.x + j : s_tlist[j]; };
+    auto advance = [&](int& k, int& j) {
+        if (++j == (SYM ? min(kC * (k + 1), n_e) : n_act)) {
+            j = 0;
+            ++k;
+        }
+    };
+
+    // Stage windows, kTableBatch at a time into a ring of kTableStages.
+    auto fill_table = [&](int base) {
+        const int q = base + tid;
+        if (tid < kTableBatch && q < n_stages) {
+            int k, j;
+            locate(q, k, j);
+            const int t = tx_of(j);
+            const int rr0 = er.x + k * kC, rrl = min(rr0 + kC - 1, er.y);
+            const TxInfo& ti = a.tx[t];
+            float mn = 3.0e38f, mx = -3.0e38f;
+            for (int rr = SYM ? max(rr0, t) : rr0; rr <= rrl; ++rr) {
+                const float2 bd = pair_bounds<MODE>(g, ti, rr, tg.xlo, tg.xhi, tg.zlo, tg.zhi);
+                mn = fminf(mn, bd.x);
+                mx = fmaxf(mx, bd.y);
+            }
+            const DF txref = tx_ref<MODE>(ti, tg.cx, tg.cz,
+                                          MODE == 0 ? elem_R(el[ti.e - er.x]) : DF{0.0f, 0.0f});
+            st[q & (kTableStages - 1)] = make_stage(a, mn, mx, txref, elem_R(el[rr0 - er.x]));
+        }
+    };
+    // TMA producer (thread 0): raw windows of stage qq into ring slot qq % ring.
+    auto issue = [&](int qq) {
+        const StageInfo si = st[qq & (kTableStages - 1)];
+        unsigned long long* bar = &s_bar[qq % ring];
+        int k, j;
+        locate(qq, k, j);
+        const int t = tx_of(j);
+        const int rr0 = er.x + k * kC, nrow = min(rr0 + kC - 1, er.y) - rr0 + 1;
+        const int na = max(si.lo, 0), nb = min(si.lo + si.len + 8, a.ns);
+        if (si.skip() || nb <= na) {
+            mbar_arrive_expect(bar, 0u);
+            return;
+        }
+        const int ca = SYM ? max(t - rr0, 0) : 0;       // first chunk row paired with t
+        const int cb = SYM ? max(t - rr0 + 1, 0) : nrow; // first row with a mirrored trace
+        const unsigned bytes = (unsigned)((nb - na) * (int)sizeof(T));
+        fence_async_shared();
+        mbar_arrive_expect(bar, bytes * (unsigned)((nrow - ca) + (nrow - cb)));
+        T* slot = raw + (size_t)(qq % ring) * kRawRows * RW;
+        const long long E = g.n_elements;
+        const T* src = rf + ((long long)t * E + rr0) * a.ns + na;   // trace (t, rr0 + c)
+        for (int c = ca; c < nrow; ++c)
+            bulk_copy_g2s(slot + c * RW + (na - si.lo), src + (long long)c * a.ns, bytes, bar);
+        if (SYM) {
+            const T* srcb = rf + ((long long)rr0 * E + t) * a.ns + na;   // trace (rr0 + c, t)
+            for (int c = cb; c < nrow; ++c)
+                bulk_copy_g2s(slot + (kC + c) * RW + (na - si.lo), srcb + (long long)c * E * a.ns, bytes, bar);
+        }
+    };
+    const int ahead = TMA ? ring - 1 : 1;   // stages in flight ahead of the one being converted
+    fill_table(0);
+
+    // PWI: range of the transmit correction ux sin + uz cos over this warp's pixels.
+    const float wux0 = (float)(WCOL * warp) * g.gdx, wux1 = (float)(WCOL * warp + WCOL - 1) * g.gdx;
+    const float wuz1 = (float)(S::kRows - 1) * g.gdz;
+
+    float acc[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) acc[p] = 0.0f;
+    float Dr[kC][P], Wr[kC][P];
+    float dr_min = 0.0f, dr_max = 0.0f;
+    unsigned cmask = 0u;
+    RegStage<T, SYM> rs;
+
+    int k = k_a, j = 0;     // stage q
+    int k1 = k_a, j1 = 0;   // stage q + 1 (register path)
+    __syncthreads();
+    if (n_stages > 0) {
+        advance(k1, j1);
+        if (TMA) {
+            if (tid == 0)
+                for (int qq = 0; qq < min(ahead, n_stages); ++qq) issue(qq);
+        } else {
+            const StageInfo s0 = st[0];
+            const int rr0 = er.x + k_a * kC;
+            if (!s0.skip()) stage_prefetch<T, SYM>(rs, a, rf, s0, tx_of(0), rr0, min(rr0 + kC - 1, er.y), vec_ok);
+        }
+    }
+
+    for (int q = 0; q < n_stages; ++q) {
+        const int r0 = er.x + k * kC;
+        const int r_last = min(r0 + kC - 1, er.y);
+        const int t = tx_of(j);
+        const StageInfo si = st[q & (kTableStages - 1)];
+        float2* buf = buf0 + (DB ? (q & 1) * kC * a.W : 0);
+        if (si.over() && tid == 0) flag(a.hdr, 1u, (unsigned)blockIdx.x, (unsigned)si.over(), (unsigned)a.W);
+        bool stuck = false;
+        if (TMA) {
+            stuck = !mbar_wait_bounded(&s_bar[q % ring], (unsigned)((q / ring) & 1));
+            if (!stuck && !si.skip()) {
+                // raw slot -> FP32 pairs, segment (trace c, block kk) = (tid >> 6 [+4], tid & 63)
+                const T* slot = raw + (size_t)(q % ring) * kRawRows * RW;
+                const int nseg = si.len >> 3, kk = tid & 63;
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    const int c = (tid >> 6) + 4 * i;
+                    if (kk >= nseg) continue;
+                    float2* dst = buf + c * a.W + 8 * kk;
+                    const bool on = r0 + c <= r_last && (!SYM || r0 + c >= t);
+                    if (!on) {
+                        zero_segment(dst);
+                    } else {
+                        Seg<T> sa;
+                        seg_load_smem<T>(sa, slot + c * RW, kk);
+                        if (SYM && r0 + c > t) {
+                            Seg<T> sb;
+                            seg_load_smem<T>(sb, slot + (kC + c) * RW, kk);
+                            seg_store_sum<T>(sa, sb, dst, si.lo + 8 * kk, a.ns);
+                        } else {
+                            seg_store<T>(sa, dst, si.lo + 8 * kk, a.ns);
+                        }
+                    }
+                }
+            }
+        } else if (!si.skip()) {
+            stage_store<T, SYM>(rs, buf, a, si, t, r0, r_last);
+        }
+        // pairs of stage q visible; raw slot of stage q - 1 and (double-buffered) pairs of q - 1 free
+        if (__syncthreads_or(stuck)) {
+            // A copy never completed: record it, let the copies still in flight land
+            // (bounded), and leave the stage loop together.
+            if (tid == 0) {
+                flag(a.hdr, 4u, (unsigned)blockIdx.x, (unsigned)q, 0u);
+                for (int qq = q + 1; qq < min(q + ahead, n_stages); ++qq)
+                    mbar_wait_bounded(&s_bar[qq % ring], (unsigned)((qq / ring) & 1));
+            }
+            break;
+        }
+        if (q + ahead < n_stages) {
+            if (((q + ahead) & (kTableBatch - 1)) == 0) {
+                fill_table(q + ahead);
+                __syncthreads();
+            }
+            if (TMA) {
+                if (tid == 0) issue(q + ahead);
+            } else {
+                const StageInfo s1 = st[(q + 1) & (kTableStages - 1)];
+                const int rr0 = er.x + k1 * kC;
+                if (!s1.skip()) stage_prefetch<T, SYM>(rs, a, rf, s1, tx_of(j1), rr0, min(rr0 + kC - 1, er.y), vec_ok);
+            }
+        }
+        if (j == 0) {
+            // New receive chunk: which elements weigh on this warp, and (only for those)
+            // window-relative distances C_c + delta and weights (times the int16 scale).
+            cmask = 0u;
+#pragma unroll
+            for (int c = 0; c < kC; ++c)
+                if (r0 + c <= r_last && r0 + c >= wr.x && r0 + c <= wr.y) cmask |= 1u << c;
+            if (cmask) {
+                const Elem e0 = el[r0 - er.x];
+                float mn = 3.0e38f, mx = -3.0e38f;
+#pragma unroll
+                for (int c = 0; c < kC; ++c) {
+                    const bool on = (cmask >> c) & 1u;
+                    const Elem ee = el[(on ? r0 + c : r0) - er.x];
+                    const float cc = elem_rel(ee, e0);
+#pragma unroll
+                    for (int p = 0; p < P; ++p) {
+                        Dr[c][p] = on ? cc + dist_delta(ee, ux, kz[p]) : 0.0f;
+                        Wr[c][p] = on ? apod_w(g.apod, -(ee.ax + ux), kap[p]) * (ee.g * a.rf_scale) : 0.0f;
+                        if (on) {
+                            mn = fminf(mn, Dr[c][p]);
+                            mx = fmaxf(mx, Dr[c][p]);
+                        }
+                    }
+                }
+                dr_min = warp_min(mn);
+                dr_max = warp_max(mx);
+            }
+        }
+        // Warp-level skip: transmit or chunk outside this warp's aperture, or every
+        // delay of the warp outside the record (tested only for windows that cross
+        // an end of the record).
+        unsigned cm = cmask;
+        if (SYM && t > r0) cm &= ~((1u << (t - r0)) - 1u);   // pairs below the diagonal
+        bool live = !si.skip() && cm != 0u;
+        if (MODE == 0) live = live && a.tx[t].e >= wr.x && a.tx[t].e <= wr.y;
+        float tw[P], wt[P];
+        if (live) {
+            if (MODE == 0) {
+                const Elem et = el[a.tx[t].e - er.x];
+                float mn = 3.0e38f, mx = -3.0e38f;
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    tw[p] = si.B + dist_delta(et, ux, kz[p]);
+                    wt[p] = apod_w(g.apod, -(et.ax + ux), kap[p]) * et.g;
+                    mn = fminf(mn, tw[p]);
+                    mx = fmaxf(mx, tw[p]);
+                }
+                if (si.edge()) {
+                    mn = warp_min(mn);
+                    mx = warp_max(mx);
+                    live = ((float)si.lo + mn + dr_min <= (float)(a.ns - 1) + 0.5f) &&
+                           ((float)si.lo + mx + dr_max >= -0.5f);
+                }
+            } else {
+                const float sn = a.tx[t].sin_f, cs = a.tx[t].cos_f;
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    tw[p] = si.B + fmaf(ux, sn, uz[p] * cs);
+                    wt[p] = 1.0f;
+                }
+                if (si.edge()) {
+                    const float v0 = wux0 * sn, v1 = wux1 * sn, z1 = wuz1 * cs;
+                    const float lo_f = (float)si.lo + si.B;
+                    live = (lo_f + fminf(v0, v1) + fminf(0.0f, z1) + dr_min <= (float)(a.ns - 1) + 0.5f) &&
+                           (lo_f + fmaxf(v0, v1) + fmaxf(0.0f, z1) + dr_max >= -0.5f);
+                }
+            }
+        }
+        if (live) {
+            float acct[P];
+#pragma unroll
+            for (int p = 0; p < P; ++p) acct[p] = 0.0f;
+#pragma unroll
+            for (int c = 0; c < kC; ++c) {
+                if (!((cm >> c) & 1u)) continue;
+                const float2* bc = buf + c * a.W;
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    const float s = tw[p] + Dr[c][p];
+                    const float m = __fadd_rd(s, kMagic);
+                    const float f = s - (m - kMagic);
+                    int idx = __float_as_int(m) - kMagicBits;
+                    if (CHECK && (idx < 0 || idx >= si.len)) {
+                        flag(a.hdr, 2u, (unsigned)blockIdx.x, (unsigned)idx, (unsigned)si.len);
+                        idx = 0;
+                    }
+                    const float2 ab = bc[idx];
+                    acct[p] = fmaf(Wr[c][p], fmaf(f, ab.y, ab.x), acct[p]);
+                }
+            }
+#pragma unroll
+            for (int p = 0; p < P; ++p) acc[p] = MODE == 0 ? fmaf(wt[p], acct[p], acc[p]) : acc[p] + acct[p];
+        }
+        if (!DB) __syncthreads();   // single buffer: compute of stage q done before stage q + 1 lands
+        k = k1;
+        j = j1;
+        advance(k1, j1);
+    }
+
+    // Partial tile in thread order: [p][tid].
+    float* dst = a.part + ((long long)b * a.n_items + item) * (kThreads * P);
+#pragma unroll
+    for (int p = 0; p < P; ++p) dst[p * kThreads + tid] = acc[p];
+}
+
+// Sum the chunk-group partials of every pixel in group order.
+template <int WCOL, int P>
+__global__ void das_reduce_kernel(const float* __restrict__ part, float* __restrict__ out, int nz,
+                                  int nx, int tiles_x, int tiles_z, int n_groups, int n_items) {
+    using S = Shape<WCOL, P>;
+    const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+    const int iz = blockIdx.y;
+    const int b = blockIdx.z;
+    if (ix >= nx) return;
+    const int rank = tile_rank(iz / S::kRows, ix / S::kCols, tiles_z, tiles_x);
+    const int cl = ix % S::kCols, rl = iz % S::kRows;
+    const int tid = (cl / WCOL) * 32 + (rl % S::kLR) * WCOL + (cl % WCOL);
+    const int local = (rl / S::kLR) * kThreads + tid;
+    const float* p = part + ((long long)b * n_items + (long long)rank * n_groups) * (kThreads * P) + local;
+    float s = 0.0f;
+    for (int k = 0; k < n_groups; ++k) s += p[(long long)k * (kThreads * P)];
+    out[((long long)b * nz + iz) * nx + ix] = s;
+}
+
+// Direct per-pixel gather for geometries whose staging windows do not fit in
+// shared memory (very coarse grids).  Each pixel is its own reference point:
+// delays in double-float, interpolation and sums in FP32.
+template <int MODE, typename T>
+__global__ void __launch_bounds__(256) das_direct_kernel(const __grid_constant__ DasArgs a) {
+    const Geom& g = a.g;
+    const int ix = blockIdx.x * 32 + (threadIdx.x & 31);
+    const int iz = blockIdx.y * 8 + (threadIdx.x >> 5);
+    const int b = blockIdx.z;
+    if (ix >= g.nx || iz >= g.nz) return;
+    const T* rf = reinterpret_cast<const T*>(a.rf) + (long long)b * a.frame_elems;
+    const DF px = df_axpk(a.gd.gx0, ix, a.gd.gdx), pz = df_axpk(a.gd.gz0, iz, a.gd.gdz);
+    const DF pz2 = df_mul(pz, pz);
+    const float kap = aperture_kappa(g, pz.hi);
+    const int2 er = tile_elements(g, px.hi, px.hi, pz.hi);
+    auto dist = [&](int e, float& dxe) {
+        const DF d = df_add(df_axpk(a.gd.xe0, e, a.gd.pitch), df_neg(px));
+        dxe = d.hi;
+        return df_sqrt(df_add(df_mul(d, d), pz2));
+    };
+    float acc = 0.0f;
+    for (int t = 0; t < a.n_tx; ++t) {
+        const TxInfo& ti = a.tx[t];
+        DF dt;
+        float wt;
+        if (MODE == 0) {
+            float dxe;
+            dt = df_add(dist(ti.e, dxe), df_neg(ti.t0));
+            wt = apod_w(g.apod, dxe, kap);
+            if (g.elem_weight) wt *= __ldg(g.elem_weight + ti.e);
+        } else {
+            dt = df_add(df_add(df_mul(px, ti.sin), df_mul(pz, ti.cos)), df_neg(ti.t0));
+            wt = 1.0f;
+        }
+        if (wt == 0.0f) continue;
+        float inner = 0.0f;
+        for (int r = er.x; r <= er.y; ++r) {
+            float dxe;
+            const DF dr = dist(r, dxe);
+            float w = apod_w(g.apod, dxe, kap);
+            if (g.elem_weight) w *= __ldg(g.elem_weight + r);
+            if (w == 0.0f) continue;
+            const DF sd = df_add(dt, dr);
+            float fl = floorf(sd.hi);
+            float f = (sd.hi - fl) + sd.lo;
+            if (f < 0.0f) { fl -= 1.0f; f += 1.0f; }
+            if (f >= 1.0f) { fl += 1.0f; f -= 1.0f; }
+            if (!(fl >= 0.0f) || !(fl <= (float)(a.ns - 2))) continue;
+            const T* tr = rf + ((long long)t * g.n_elements + r) * a.ns + (int)fl;
+            const float x0 = raw_one<T>(raw_bits<T>(tr)), x1 = raw_one<T>(raw_bits<T>(tr + 1));
+            inner = fmaf(w, fmaf(f, x1 - x0, x0), inner);
+        }
+        acc = fmaf(wt, inner, acc);
+    }
+    a.out[((long long)b * g.nz + iz) * g.nx + ix] = acc * a.rf_scale;
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launch plan and launchers (instantiated per mode and bounds-check
+// variant in their own translation units).
+// ---------------------------------------------------------------------------
+struct Cfg {
+    int wcol, p;
+};
+
+struct Plan {
+    Cfg cfg;
+    int cols, rows;
+    int tiles_x, tiles_z, n_groups, n_items;
+    int W, ring;
+    bool tiled, db, tma, sym;
+    size_t smem;
+    size_t ws_bytes;
+};
+
+constexpr size_t kMaxTiledSmem = 220 * 1024;  // one CTA per SM
+
+template <int MODE, typename T, int WCOL, int P, bool DB, bool TMA, bool CHECK, bool SYM>
+wf_status launch_tiled_v(DasArgs& A, const Plan& PL, int batch, cudaStream_t st) {
+    static unsigned long long smem_set = 0ull;
+    auto kern = das_tiled_kernel<MODE, T, WCOL, P, DB, TMA, CHECK, SYM>;
+    wf_status s = ensure_smem_limit(kern, kMaxTiledSmem, smem_set);
+    if (s != WF_OK) return s;
+    kern<<<dim3(PL.n_items, batch), kThreads, PL.smem, st>>>(A);
+    if ((s = last_launch_status()) != WF_OK) return s;
+    dim3 rg((A.g.nx + 127) / 128, A.g.nz, batch);
+    das_reduce_kernel<WCOL, P><<<rg, 128, 0, st>>>(A.part, A.out, A.g.nz, A.g.nx, PL.tiles_x,
+                                                   PL.tiles_z, PL.n_groups, PL.n_items);
+    return last_launch_status();
+}
+
+template <int MODE, typename T, int WCOL, int P, bool CHECK, bool SYM>
+wf_status launch_tiled(DasArgs& A, const Plan& PL, int batch, cudaStream_t st) {
+    if (!PL.tma) return launch_tiled_v<MODE, T, WCOL, P, false, false, CHECK, SYM>(A, PL, batch, st);
+    return PL.db ? launch_tiled_v<MODE, T, WCOL, P, true, true, CHECK, SYM>(A, PL, batch, st)
+                 : launch_tiled_v<MODE, T, WCOL, P, false, true, CHECK, SYM>(A, PL, batch, st);
+}
+
+template <int MODE, typename T, bool CHECK, bool SYM>
+wf_status launch_tiled_cfg(DasArgs& A, const Plan& P, int batch, cudaStream_t st) {
+    return P.cfg.p == 4 ? launch_tiled<MODE, T, 4, 4, CHECK, SYM>(A, P, batch, st)
+                        : launch_tiled<MODE, T, 4, 2, CHECK, SYM>(A, P, batch, st);
+}
+
+// Reverse-mode launcher (das_grad.cu): derivatives of <grad_out, DAS(rf)> with
+// respect to the RF, the element weights and the sound speed.
+template <int MODE>
+wf_status launch_das_backward(DasArgs& A, const Plan& P, int batch, bool need_rf, bool need_par,
+                              cudaStream_t st);
+
+// Tiled launch of one mode and bounds-check variant, every RF type.
+template <int MODE, bool CHECK>
+wf_status launch_das_tiled(DasArgs& A, const Plan& P, int batch, wf_dtype dt, cudaStream_t st) {
+    switch (dt) {
+        case WF_F32:
+            return P.sym ? launch_tiled_cfg<MODE, float, CHECK, MODE == 0>(A, P, batch, st)
+                         : launch_tiled_cfg<MODE, float, CHECK, false>(A, P, batch, st);
+        case WF_F16:
+            return P.sym ? launch_tiled_cfg<MODE, __half, CHECK, MODE == 0>(A, P, batch, st)
+                         : launch_tiled_cfg<MODE, __half, CHECK, false>(A, P, batch, st);
+        case WF_I16:
+            return P.sym ? launch_tiled_cfg<MODE, int16_t, CHECK, MODE == 0>(A, P, batch, st)
+                         : launch_tiled_cfg<MODE, int16_t, CHECK, false>(A, P, batch, st);
+    }
+    return WF_ERR_INVALID_ARG;
+}
+
+}  // namespace wf

@@ -45,6 +45,7 @@ SWEEP = [
     ("stai", "f32", 1, 1, 600, 5, 3, configs.NONE, False, 0.0, 1),
     ("stai", "f32", 12, 3, 2, 9, 9, configs.HANN, False, 0.0, 1),
     ("stai", "f32", 33, 33, 640, 1, 1, configs.HANN, False, 0.0, 1),
+    ("stai", "f16", 24, 24, 904, 70, 50, configs.HANN, True, 1e-6, 2),
     ("pwi", "f32", 16, 5, 700, 37, 45, configs.HANN, False, 0.0, 1),
     ("pwi", "f16", 24, 9, 900, 64, 64, configs.HANN, True, 1.0, 2),
     ("pwi", "i16", 20, 1, 1000, 33, 31, configs.RECT, False, 0.0, 3),
@@ -59,6 +60,45 @@ def test_random_rf_sweep_parity(k):
     case = configs.random_case(mode, seed=100 + k, n_elements=e, n_tx=n_tx,
                                n_samples=ns, nz=nz, nx=nx, dtype=dtype, apod=apod,
                                elem_weight=weights, t_start=t0, batch=batch)
+    _assert_parity(case)
+
+
+STAGING_VARIANTS = [
+    {},                                              # default: reciprocal pairs, TMA staging
+    {"WF_DAS_NO_SYM": "1"},                          # every (t, r) pair on its own trace
+    {"WF_DAS_NO_TMA": "1"},                          # register-staged path, reciprocal
+    {"WF_DAS_NO_TMA": "1", "WF_DAS_NO_SYM": "1"},
+    {"WF_DAS_TILE": "4,2"},                          # 32 x 16 tiles
+    {"WF_DAS_TILE": "4,2", "WF_DAS_NO_SYM": "1"},
+]
+
+
+@pytest.mark.parametrize("mode", ["stai", "pwi"])
+def test_staging_variants_agree_with_oracle(mode, monkeypatch):
+    """Every staging path and tile shape the planner can pick, on one geometry."""
+    case = configs.random_case(mode, seed=21, n_elements=32, n_tx=32 if mode == "stai" else 7,
+                               n_samples=1024, nz=96, nx=80, dtype="i16", elem_weight=True,
+                               t_start=1e-6 if mode == "stai" else 1.0)
+    want = oracle.das(case, threads=THREADS)
+    outs = []
+    for env in STAGING_VARIANTS:
+        for k in ("WF_DAS_NO_SYM", "WF_DAS_NO_TMA", "WF_DAS_TILE"):
+            monkeypatch.delenv(k, raising=False)
+        for k, v in env.items():
+            monkeypatch.setenv(k, v)
+        got = das_gpu(case).cpu().numpy()[0]
+        assert rel_l2(got, want) <= TOL_BF_REL_L2, env
+        outs.append(got)
+    # the same sums up to FP32 rounding of delays (tile reference points) and order
+    for o in outs[1:]:
+        assert rel_l2(o, outs[0]) <= 3e-5
+
+
+def test_stai_permuted_transmit_order_matches_oracle():
+    """All elements fire, but not in element order: the general (non-reciprocal) path."""
+    case = configs.random_case("stai", seed=22, n_elements=24, n_tx=24, n_samples=800,
+                               nz=48, nx=40, dtype="f32")
+    case.tx_elem = np.random.default_rng(5).permutation(24).astype(np.int32)
     _assert_parity(case)
 
 

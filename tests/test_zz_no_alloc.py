@@ -44,7 +44,7 @@ def test_fixed_scratch_size_is_exported_and_oversized_requests_are_refused():
     assert cap == 32 << 20
     case = configs.random_case("stai", 1, n_elements=128, n_tx=128, n_samples=2048, nz=512, nx=256)
     pr, gr = _probe_grid(case)
-    batch = 16
+    batch = 128
     assert wf.das_workspace_bytes(pr, gr, batch, 128) > cap
     # refused on the host, before any device call: dummy (aligned) pointers are never touched
     st = lib.wf_das_stai_fixed_scratch(C.byref(pr._c()), C.byref(gr._c()), batch, 128, None, 128,
