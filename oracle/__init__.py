@@ -96,6 +96,12 @@ def _load():
             lib.or_das_backward.argtypes = [P, G, C.c_int32, C.c_int32, ip, dp, dp, C.c_int32,
                                             C.c_int32, dp, dp, C.c_int32, C.c_int32, dp, dp, dp]
             lib.or_das_backward.restype = C.c_int
+            lib.or_envelope_backward.argtypes = [dp, C.c_int32, C.c_int32, dp, C.c_int32, C.c_int32,
+                                                 dp]
+            lib.or_envelope_backward.restype = None
+            lib.or_logclip_backward.argtypes = [dp, C.c_int64, C.c_double, C.c_int32, C.c_double,
+                                                C.c_double, dp, dp]
+            lib.or_logclip_backward.restype = None
             _lib = lib
     return _lib
 
@@ -368,6 +374,37 @@ def das_backward_case(case, y, frame: int = 0, threads: int = 1, need=("rf", "g"
                             t_start=case.t_start, threads=threads, need=need)
     return das_backward(case.rf64[frame], pr, gr, y, mode="pwi", angles=case.angles,
                         t_starts=case.t_starts, threads=threads, need=need)
+
+
+def envelope_backward(bf, g_env, threads: int = 1) -> np.ndarray:
+    """Cotangent of bf [nz][nx] for a cotangent g_env of envelope(bf)."""
+    b, g = _f64(bf), _f64(g_env)
+    nz, nx = b.shape
+    out = np.zeros_like(b)
+    lib = _load()
+    n = max(1, min(threads, nx))
+    step = -(-nx // n)
+    chunks = [(a, min(nx, a + step)) for a in range(0, nx, step)]
+
+    def run(ab):
+        lib.or_envelope_backward(_dp(b), nz, nx, _dp(g), ab[0], ab[1], _dp(out))
+
+    if len(chunks) == 1:
+        run(chunks[0])
+    else:
+        with ThreadPoolExecutor(len(chunks)) as ex:
+            list(ex.map(run, chunks))
+    return out
+
+
+def logclip_backward(env, g_db, ref=None, lo=-60.0, hi=0.0) -> np.ndarray:
+    """Cotangent of env for a cotangent g_db of logclip(env, ref, lo, hi); ref None = the
+    frame maximum, whose cotangent then goes to the first pixel attaining it."""
+    e, g = _f64(env), _f64(g_db)
+    r = frame_max(e) if ref is None else float(ref)
+    out = np.zeros_like(e)
+    _load().or_logclip_backward(_dp(e), e.size, r, int(ref is None), lo, hi, _dp(g), _dp(out))
+    return out
 
 
 def das(case, frame: int = 0, threads: int = 1, rows=None) -> np.ndarray:

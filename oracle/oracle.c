@@ -388,3 +388,74 @@ void or_logclip(const double* env, int64_t n, double ref, double lo, double hi, 
         out[i] = db < lo ? lo : (db > hi ? hi : db);
     }
 }
+
+/*
+ * Reverse mode of the envelope (Fig. 2 "Analytic Signal" -> "Absolute
+ * Value").  Per column, z = A b with A = F^-1 diag(H) F (F the DFT matrix, H
+ * the one-sided-spectrum mask above) and env = |z|.  For a cotangent g of env
+ * the cotangent of z is g z / |z| (0 where |z| = 0), and since b is real the
+ * cotangent of b is Re(A^H g_z) with A^H = F^H diag(H) F^-H, F^-H = F / N and
+ * F^H = N F^-1: evaluated here literally as N IDFT(H (DFT(g_z) / N)).
+ * Columns [col_begin, col_end) of g_bf[nz][nx] are written.
+ */
+void or_envelope_backward(const double* bf, int32_t nz, int32_t nx, const double* g_env,
+                          int32_t col_begin, int32_t col_end, double* g_bf)
+{
+    double* buf = (double*)malloc(sizeof(double) * (size_t)nz * 7);
+    double* col = buf;
+    double* zr = col + nz;
+    double* zi = zr + nz;
+    double* gr = zi + nz;
+    double* gi = gr + nz;
+    double* yr = gi + nz;
+    double* yi = yr + nz;
+    for (int32_t ix = col_begin; ix < col_end; ++ix) {
+        for (int32_t iz = 0; iz < nz; ++iz) col[iz] = bf[(size_t)iz * nx + ix];
+        or_analytic(col, nz, zr, zi);
+        for (int32_t iz = 0; iz < nz; ++iz) {
+            double m = sqrt(zr[iz] * zr[iz] + zi[iz] * zi[iz]);
+            double g = g_env[(size_t)iz * nx + ix];
+            gr[iz] = m > 0.0 ? g * zr[iz] / m : 0.0;
+            gi[iz] = m > 0.0 ? g * zi[iz] / m : 0.0;
+        }
+        or_dft(gr, gi, nz, 0, yr, yi);                  /* F g_z */
+        for (int32_t k = 0; k < nz; ++k) {
+            double h;
+            if (k == 0) h = 1.0;
+            else if (2 * k < nz) h = 2.0;
+            else if (2 * k == nz) h = 1.0;
+            else h = 0.0;
+            yr[k] *= h / (double)nz;                    /* diag(H) F^-H g_z */
+            yi[k] *= h / (double)nz;
+        }
+        or_dft(yr, yi, nz, 1, gr, gi);                  /* F^-1 (.) ; F^H = N F^-1 */
+        for (int32_t iz = 0; iz < nz; ++iz) g_bf[(size_t)iz * nx + ix] = (double)nz * gr[iz];
+    }
+    free(buf);
+}
+
+/*
+ * Reverse mode of the dynamic adjustment out = clamp(20 log10(max(env,
+ * 1e-30 ref) / ref), lo, hi).  Where the value is strictly inside (lo, hi)
+ * and env > 1e-30 ref, d out / d env = 20 / (ln 10 env) and d out / d ref =
+ * -20 / (ln 10 ref); elsewhere (clipped, floored, NaN, ref <= 0) both are 0.
+ * When ref_is_max, ref is the frame maximum of env and its cotangent is added
+ * to the first pixel that attains it.  Writes g_env[n].
+ */
+void or_logclip_backward(const double* env, int64_t n, double ref, int32_t ref_is_max, double lo,
+                         double hi, const double* g_db, double* g_env)
+{
+    double s_ref = 0.0;
+    int64_t arg = -1;
+    for (int64_t i = 0; i < n; ++i) {
+        double v = env[i];
+        g_env[i] = 0.0;
+        if (arg < 0 && v == ref) arg = i;
+        if (v != v || !(ref > 0.0) || !(v > 1e-30 * ref)) continue;
+        double db = 20.0 * log10(v / ref);
+        if (!(db > lo && db < hi)) continue;
+        g_env[i] = g_db[i] * 20.0 / (log(10.0) * v);
+        s_ref += g_db[i] * (-20.0 / (log(10.0) * ref));
+    }
+    if (ref_is_max && arg >= 0) g_env[arg] += s_ref;
+}

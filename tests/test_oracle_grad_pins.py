@@ -1,4 +1,5 @@
-"""Pins of the oracle's reverse-mode DAS derivatives (oracle.or_das_backward).
+"""Pins of the oracle's reverse-mode derivatives (das_backward, envelope_backward,
+logclip_backward).
 
 Each derivative is pinned to something other than its own loop:
   * grad_rf by the adjoint identity <DAS x, y> = <x, DAS^T y> against the
@@ -8,7 +9,10 @@ Each derivative is pinned to something other than its own loop:
     difference is exact up to rounding for any step;
   * grad_c by central finite differences of the FP64 forward with a step so
     small (1e-10 relative) that essentially no delay crosses a sample boundary;
-  * a single-term geometry whose derivatives are written out by hand.
+  * a single-term geometry whose derivatives are written out by hand;
+  * the envelope and log-clip cotangents by central differences of their
+    forwards (both smooth away from |z| = 0 and from the clip limits), with the
+    frame maximum's cotangent reaching every unclipped pixel.
 All CPU, small sizes.
 """
 import math
@@ -136,3 +140,39 @@ def test_window_is_apod_without_weight():
             w = oracle.window(pr, x, z, e)
             assert math.isclose(w * pr.elem_weight[e], oracle.apod(pr, x, z, e), rel_tol=1e-14,
                                 abs_tol=1e-300)
+
+
+def test_envelope_backward_matches_central_difference():
+    rng = np.random.default_rng(31)
+    nz, nx = 32, 5
+    bf = rng.standard_normal((nz, nx))
+    g = rng.standard_normal((nz, nx))
+    got = oracle.envelope_backward(bf, g)
+    h = 1e-6
+    for iz, ix in [(0, 0), (5, 1), (16, 2), (17, 3), (31, 4), (9, 0)]:
+        bp, bm = bf.copy(), bf.copy()
+        bp[iz, ix] += h
+        bm[iz, ix] -= h
+        fd = (np.sum(g * oracle.envelope(bp)) - np.sum(g * oracle.envelope(bm))) / (2 * h)
+        assert abs(fd - got[iz, ix]) <= 1e-6 * (1.0 + abs(got[iz, ix])), (iz, ix, fd, got[iz, ix])
+
+
+def test_logclip_backward_matches_central_difference_including_the_frame_max():
+    rng = np.random.default_rng(32)
+    env = rng.uniform(1e-4, 1.0, size=(20, 12))
+    env[3, 4] = 2.0                     # the frame maximum (its cotangent reaches every pixel)
+    env[7, 7] = 1e-5                    # clipped at -60 dB: no derivative
+    g = rng.standard_normal(env.shape)
+    got = oracle.logclip_backward(env, g)
+    assert got[7, 7] == 0.0
+    h = 1e-7
+    for iz, ix in [(3, 4), (0, 0), (10, 5), (19, 11)]:
+        ep, em = env.copy(), env.copy()
+        ep[iz, ix] += h
+        em[iz, ix] -= h
+        fd = (np.sum(g * oracle.logclip(ep)) - np.sum(g * oracle.logclip(em))) / (2 * h)
+        assert abs(fd - got[iz, ix]) <= 1e-6 * (1.0 + abs(got[iz, ix])), (iz, ix, fd, got[iz, ix])
+    # with a caller reference nothing flows to the maximum except its own (clipped) value
+    got_ref = oracle.logclip_backward(env, g, ref=2.0)
+    assert got_ref[3, 4] == 0.0
+    assert math.isclose(got_ref[0, 0], g[0, 0] * 20 / (math.log(10) * env[0, 0]), rel_tol=1e-13)

@@ -57,6 +57,15 @@ MUTANTS = {
     "grad_c_t_start_dropped": ("double dsdc = -(s + t0 * p->fs) / p->c;", "double dsdc = -s / p->c;",
                                ["test_sound_speed_gradient_matches_central_difference",
                                 "test_single_term_by_hand"]),
+    "env_bwd_missing_1_over_n": ("yr[k] *= h / (double)nz;", "yr[k] *= h;",
+                                 ["test_envelope_backward_matches_central_difference"]),
+    "env_bwd_imag_dropped": ("gi[iz] = m > 0.0 ? g * zi[iz] / m : 0.0;", "gi[iz] = 0.0;",
+                             ["test_envelope_backward_matches_central_difference"]),
+    "logclip_bwd_natural_log": ("g_env[i] = g_db[i] * 20.0 / (log(10.0) * v);",
+                                "g_env[i] = g_db[i] * 20.0 / v;",
+                                ["test_logclip_backward_matches_central_difference_including_the_frame_max"]),
+    "logclip_bwd_ref_dropped": ("if (ref_is_max && arg >= 0) g_env[arg] += s_ref;", "",
+                                ["test_logclip_backward_matches_central_difference_including_the_frame_max"]),
     "window_width": ("double half_width = 0.5 * z / p->f_number;", "double half_width = z / p->f_number;",
                      ["test_window_is_apod_without_weight", "test_adjoint_identity"]),
 }
