@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--workload", default="stai_full",
                     choices=["stai_full", "stai_small", "pwi_full_i16", "pwi_full_f16", "pwi_batch",
-                             "served"])
+                             "served", "diff_pwi"])
     ap.add_argument("--rate", type=float, default=200.0, help="served: Poisson arrival rate (req/s)")
     ap.add_argument("--requests", type=int, default=240, help="served: requests in the stream")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
@@ -62,6 +62,9 @@ WORKLOAD_TEXT = {
     "pwi_full_i16": "PWI 64 angles (-16..16 deg) x 128 rx x 4096 int16, 1024 x 512 grid",
     "pwi_full_f16": "PWI 64 angles (-16..16 deg) x 128 rx x 4096 float16, 1024 x 512 grid",
     "pwi_batch": "PWI 16 frames x 16 angles x 128 rx x 2048 float32, 512 x 256 grid 5-30 mm",
+    "diff_pwi": "differentiable PWI: 16 frames x 16 angles x 128 rx x 2048 float32, 512 x 256 grid "
+                "5-30 mm; forward DAS + envelope + log-clip, MSE against a target B-mode, backward "
+                "to the RF, 128 element weights and the speed of sound",
 }
 
 
@@ -527,6 +530,100 @@ def run_served(args):
     }
 
 
+# ----------------------------------------------------------------------------- differentiable step
+
+def run_diff(args):
+    """One training step of a differentiable beamformer per timed step (16 frames): forward
+    bmode_diff, loss = mean((db - target)^2), backward to rf, element weights and c."""
+    import paper_1811_01566_gb300 as wf
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    case = make_case("pwi_batch", str(dev))
+    b = case.batch
+    pr = wf.Probe(case.n_elements, case.pitch, case.fs, case.c, case.f_number, case.apod)
+    gr = wf.Grid(case.nz, case.nx, case.x_min, case.x_max, case.z_min, case.z_max)
+    scan = dict(angles=case.angles, t_start=case.t_starts)
+    rf = torch.from_numpy(case.rf).to(dev).requires_grad_(True)
+    w = torch.ones(case.n_elements, device=dev, requires_grad=True)
+    c = torch.tensor(case.c, device=dev, requires_grad=True)
+    with torch.no_grad():   # target: the same scan beamformed with a 2 % faster medium
+        target = wf.bmode_diff(rf.detach(), wf.Probe(pr.n_elements, pr.pitch, pr.fs, 1.02 * case.c,
+                                                      pr.f_number, pr.apod), gr, "pwi", **scan)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        rf.grad = w.grad = c.grad = None
+        db = wf.bmode_diff(rf, pr, gr, "pwi", elem_weight=w, c=c, **scan)
+        loss = torch.mean((db - target) ** 2)
+        loss.backward()
+        return loss
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize(dev)
+    if args.profile_only:
+        for _ in range(args.steps):
+            step()
+        torch.cuda.synchronize(dev)
+        return None
+    steps = min(args.steps, 200)
+    with ClockSampler(0) as clk:
+        w0 = time.time()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        clk.region(w0, time.time())
+    ms = e0.elapsed_time(e1) / steps
+    # stage split of the library calls (events on the launching stream)
+    bf = torch.empty(b, case.nz, case.nx, device=dev)
+    env = torch.empty_like(bf)
+    db = torch.empty_like(bf)
+    g = torch.empty_like(bf)
+    ws = torch.empty(wf.das_workspace_bytes(pr, gr, b, case.n_tx), dtype=torch.uint8, device=dev)
+    x = rf.detach()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(7)]
+    names = ["das", "envelope", "logclip", "logclip_backward", "envelope_backward", "das_backward"]
+    acc = dict.fromkeys(names, 0.0)
+    k = 20
+    for _ in range(k):
+        ev[0].record(stream)
+        wf.das_pwi(x, pr, gr, out=bf, workspace=ws, **scan)
+        ev[1].record(stream)
+        wf.envelope(bf, out=env, with_max=False)
+        ev[2].record(stream)
+        wf.logclip(env, out=db)
+        ev[3].record(stream)
+        wf.logclip_backward(env, db, out=g)
+        ev[4].record(stream)
+        wf.envelope_backward(bf, g, out=g)
+        ev[5].record(stream)
+        wf.das_backward(x, g, pr, gr, "pwi", **scan)
+        ev[6].record(stream)
+        torch.cuda.synchronize(dev)
+        for i, n in enumerate(names):
+            acc[n] += ev[i].elapsed_time(ev[i + 1]) / k
+    _, active, contributing, _ = delay_sum_counts(case, dev)
+    fwd_rate = contributing * b / (acc["das"] / 1e3)
+    bwd_rate = contributing * b / (acc["das_backward"] / 1e3)
+    return {
+        "metric": "differentiable B-mode training frames/s (forward + backward)",
+        "value": round(b / (ms / 1e3), 2), "unit": "frames/s", "n_gpus": 1, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"diff_pwi: {WORKLOAD_TEXT['diff_pwi']}", "frames_per_step": b,
+                   "launch": "eager autograd step (the sound speed is read on the host each step)"},
+        "stages_ms": {n: round(v, 4) for n, v in acc.items()},
+        "g_terms_per_s": {"das_forward_contributing": round(fwd_rate / 1e9, 2),
+                          "das_backward_contributing": round(bwd_rate / 1e9, 2)},
+        "delay_sums_per_frame": {"aperture_active": active, "contributing": contributing},
+        "gpu_launches": 7 * steps,
+        "clocks": clk.summary(),
+    }
+
+
 # ----------------------------------------------------------------------------- reference arm
 
 def run_reference(args):
@@ -582,6 +679,12 @@ def main():
     if args.workload == "served":
         if rank == 0:
             print(json.dumps(run_served(args)), flush=True)
+        return
+    if args.workload == "diff_pwi":
+        if rank == 0:
+            line = run_diff(args)
+            if line is not None:
+                print(json.dumps(line), flush=True)
         return
     if world > 1:
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))

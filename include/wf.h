@@ -239,6 +239,39 @@ wf_status wf_logclip(const float* env, int32_t batch, int32_t nz, int32_t nx, co
                      float db_min, float db_max, float* out_db, wf_stream stream);
 
 /*
+ * Reverse mode of wf_envelope (the differentiable B-mode path).  For a
+ * cotangent grad_env of env = |Z|, Z = A b with A = IDFT . diag(H) . DFT,
+ * the cotangent of b is Re(A^H (grad_env Z / |Z|)) (0 where |Z| = 0); A is
+ * Hermitian and Re(A r) = r for real r, so this equals
+ * Re(g) - Hilbert(Im g) with g = grad_env Z / |Z|, computed per column pair
+ * with two paired Hilbert transforms (Z is rebuilt from bf, not stored).
+ *
+ *  bf           device float [batch][nz][nx], the envelope's input
+ *  grad_env     device float [batch][nz][nx]
+ *  grad_bf      device float [batch][nz][nx]; may alias grad_env
+ */
+wf_status wf_envelope_backward(const float* bf, int32_t batch, int32_t nz, int32_t nx,
+                               const float* grad_env, float* grad_bf, wf_stream stream);
+
+/*
+ * Reverse mode of wf_logclip.  Where the output is strictly inside (db_min,
+ * db_max) and env > 1e-30 ref, d out/d env = 20 / (ln 10 env) and
+ * d out/d ref = -20 / (ln 10 ref); clipped, floored and NaN pixels pass 0.
+ * When ref is NULL (the forward used the frame maximum) or ref_is_frame_max is
+ * non-zero (the caller's ref is that maximum, e.g. wf_envelope's frame_max),
+ * the reference's cotangent is added to the first pixel (lowest index) whose
+ * envelope equals ref; otherwise ref is a constant.
+ *
+ *  env, ref, db_min, db_max   as the forward call
+ *  grad_db      device float [batch][nz][nx]
+ *  grad_env     device float [batch][nz][nx]; may alias grad_db, not env
+ */
+wf_status wf_logclip_backward(const float* env, int32_t batch, int32_t nz, int32_t nx,
+                              const float* ref, int32_t ref_is_frame_max, float db_min,
+                              float db_max, const float* grad_db, float* grad_env,
+                              wf_stream stream);
+
+/*
  * STAI delay-and-sum exactly as wf_das_stai, without a caller workspace.
  * (No counterpart in the paper: this entry point exists for callers that
  * cannot allocate device memory, such as a real-time acquisition loop whose

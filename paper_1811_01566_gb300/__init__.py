@@ -23,7 +23,8 @@ from . import _build
 
 __all__ = ["Probe", "Grid", "WfError", "HANN", "RECT", "NONE", "das_stai", "das_pwi",
            "das_workspace_bytes", "das_delays", "das_backward", "das", "envelope", "logclip",
-           "bmode", "workspace_check", "library_path", "version"]
+           "envelope_backward", "logclip_backward", "bmode", "bmode_diff", "workspace_check",
+           "library_path", "version"]
 
 HANN, RECT, NONE = 0, 1, 2
 _DTYPES = {torch.float32: 0, torch.float16: 1, torch.int16: 2}
@@ -85,6 +86,10 @@ def _load():
             lib.wf_envelope.restype = C.c_int
             lib.wf_logclip.argtypes = [vp, i32, i32, i32, vp, f32, f32, vp, vp]
             lib.wf_logclip.restype = C.c_int
+            lib.wf_envelope_backward.argtypes = [vp, i32, i32, i32, vp, vp, vp]
+            lib.wf_envelope_backward.restype = C.c_int
+            lib.wf_logclip_backward.argtypes = [vp, i32, i32, i32, vp, i32, f32, f32, vp, vp, vp]
+            lib.wf_logclip_backward.restype = C.c_int
             lib.wf_workspace_check.argtypes = [vp, sz, vp]
             lib.wf_workspace_check.restype = C.c_int
             lib.wf_status_string.argtypes = [C.c_int]
@@ -348,6 +353,82 @@ def logclip(env: torch.Tensor, *, ref: torch.Tensor | None = None, db_min: float
                             float(db_min), float(db_max), out.data_ptr(), _stream(stream))
     _check(st, "wf_logclip")
     return out
+
+
+def _frames3(t: torch.Tensor, name: str) -> torch.Tensor:
+    if t.dim() == 2:
+        t = t.unsqueeze(0)
+    if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous() and t.dim() == 3):
+        raise ValueError(f"{name} must be a contiguous CUDA float32 [batch, nz, nx] tensor")
+    return t
+
+
+def envelope_backward(bf: torch.Tensor, grad_env: torch.Tensor, *, out: torch.Tensor | None = None,
+                      stream=None) -> torch.Tensor:
+    """Cotangent of bf for a cotangent grad_env of envelope(bf); see wf_envelope_backward."""
+    bf, grad_env = _frames3(bf, "bf"), _frames3(grad_env, "grad_env")
+    if grad_env.shape != bf.shape:
+        raise ValueError("grad_env must have bf's shape")
+    b, nz, nx = bf.shape
+    out = torch.empty_like(bf) if out is None else out
+    st = _load().wf_envelope_backward(bf.data_ptr(), b, nz, nx, grad_env.data_ptr(), out.data_ptr(),
+                                      _stream(stream))
+    _check(st, "wf_envelope_backward")
+    return out
+
+
+def logclip_backward(env: torch.Tensor, grad_db: torch.Tensor, *, ref: torch.Tensor | None = None,
+                     ref_is_frame_max: bool = True, db_min: float = -60.0, db_max: float = 0.0,
+                     out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Cotangent of env for a cotangent grad_db of logclip(env, ...); see wf_logclip_backward."""
+    env, grad_db = _frames3(env, "env"), _frames3(grad_db, "grad_db")
+    if grad_db.shape != env.shape:
+        raise ValueError("grad_db must have env's shape")
+    b, nz, nx = env.shape
+    if ref is not None and not (ref.is_cuda and ref.dtype == torch.float32 and ref.numel() == b):
+        raise ValueError("ref must be a CUDA float32 [batch] tensor")
+    out = torch.empty_like(env) if out is None else out
+    st = _load().wf_logclip_backward(env.data_ptr(), b, nz, nx, None if ref is None else ref.data_ptr(),
+                                     int(bool(ref_is_frame_max)), float(db_min), float(db_max),
+                                     grad_db.data_ptr(), out.data_ptr(), _stream(stream))
+    _check(st, "wf_logclip_backward")
+    return out
+
+
+class _Envelope(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, bf):
+        env, _ = envelope(bf, with_max=False)
+        ctx.save_for_backward(bf)
+        return env
+
+    @staticmethod
+    def backward(ctx, grad_env):
+        (bf,) = ctx.saved_tensors
+        return envelope_backward(bf, grad_env.contiguous())
+
+
+class _LogClip(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, env, db_min, db_max):
+        ctx.save_for_backward(env)
+        ctx.db = (db_min, db_max)
+        return logclip(env, db_min=db_min, db_max=db_max)
+
+    @staticmethod
+    def backward(ctx, grad_db):
+        (env,) = ctx.saved_tensors
+        g = logclip_backward(env, grad_db.contiguous(), db_min=ctx.db[0], db_max=ctx.db[1])
+        return g, None, None
+
+
+def bmode_diff(rf: torch.Tensor, probe: Probe, grid: Grid, mode: str, *, elem_weight=None, c=None,
+               db_min: float = -60.0, db_max: float = 0.0, **scan) -> torch.Tensor:
+    """Differentiable Fig. 2 pipeline (float32 RF): DAS -> envelope -> log-clip with the frame
+    maximum as reference; gradients reach rf, elem_weight and c through the library's
+    reverse-mode kernels."""
+    bf = das(rf, probe, grid, mode, elem_weight=elem_weight, c=c, **scan)
+    return _LogClip.apply(_Envelope.apply(bf), float(db_min), float(db_max))
 
 
 def bmode(rf: torch.Tensor, probe: Probe, grid: Grid, *, mode: str, db_min: float = -60.0,

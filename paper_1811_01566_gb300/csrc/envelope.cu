@@ -131,6 +131,107 @@ __global__ void __launch_bounds__(kEnvThreads) envelope_kernel(const float* __re
     }
 }
 
+// Reverse mode.  The analytic-signal map A = F^-1 diag(H) F is Hermitian (H is
+// real), and for a real column Re(A r) = r and Im(A r) = Hilbert(r).  For a
+// cotangent g_env of env = |z|, z = b + i Hilbert(b), the cotangent of z is
+// g = g_env z / |z| (0 where |z| = 0) and that of the real column b is
+// Re(A^H g) = Re(A g) = Re(g) - Hilbert(Im g).  Per column pair: one paired
+// Hilbert transform rebuilds z, a second one transforms the imaginary parts.
+template <int PAIRS>
+__global__ void __launch_bounds__(kEnvThreads) envelope_backward_kernel(
+    const float* bf, const float* grad_env, float* grad_bf, int nz, int log2n, int nx) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n = nz;
+    float2* A = reinterpret_cast<float2*>(smem_raw);     // [PAIRS][n]
+    float2* B = A + PAIRS * n;                            // [PAIRS][n]
+    float2* R = B + PAIRS * n;                            // [PAIRS][n] real parts of g
+    float2* tw = R + PAIRS * n;                           // [n/2]
+    const int b = blockIdx.y;
+    const int x0 = blockIdx.x * (2 * PAIRS);
+    const long long fo = (long long)b * nz * nx;
+    const float* src = bf + fo;
+
+    for (int m = threadIdx.x; m < (n >> 1); m += blockDim.x) {
+        float s, c;
+        sincospif(2.0f * (float)m / (float)n, &s, &c);
+        tw[m] = make_float2(c, -s);
+    }
+    for (int q = threadIdx.x; q < PAIRS * n; q += blockDim.x) {
+        const int pr = q / n, z = q - pr * n;
+        const int xa = x0 + 2 * pr;
+        const float va = xa < nx ? src[(long long)z * nx + xa] : 0.0f;
+        const float vb = xa + 1 < nx ? src[(long long)z * nx + xa + 1] : 0.0f;
+        A[q] = make_float2(va, vb);
+    }
+    __syncthreads();
+    // Paired Hilbert transform of the sequences in `buf` (result n * (h_a + i h_b) in the
+    // returned buffer).
+    auto hilbert = [&](float2* in, float2* out) {
+        for (int ns = 1; ns < n; ns <<= 1) {
+            stockham_pass(in, out, tw, n, log2n, ns, PAIRS, false);
+            __syncthreads();
+            float2* t = in; in = out; out = t;
+        }
+        for (int q = threadIdx.x; q < PAIRS * n; q += blockDim.x) {
+            const int k = q & (n - 1);
+            const float2 y = in[q];
+            float2 gv;
+            if (k == 0 || 2 * k == n) gv = make_float2(0.0f, 0.0f);
+            else if (2 * k < n) gv = make_float2(y.y, -y.x);
+            else gv = make_float2(-y.y, y.x);
+            in[q] = gv;
+        }
+        __syncthreads();
+        for (int ns = 1; ns < n; ns <<= 1) {
+            stockham_pass(in, out, tw, n, log2n, ns, PAIRS, true);
+            __syncthreads();
+            float2* t = in; in = out; out = t;
+        }
+        return in;
+    };
+    float2* h = hilbert(A, B);
+    float2* other = h == A ? B : A;
+    const float inv_n = 1.0f / (float)n;
+    // g = g_env z / |z|: real parts to R, imaginary parts (the next transform's input) to `other`.
+    for (int q = threadIdx.x; q < PAIRS * n; q += blockDim.x) {
+        const int pr = q / n, z = q - pr * n;
+        const int xa = x0 + 2 * pr;
+        float2 re = make_float2(0.0f, 0.0f), im = make_float2(0.0f, 0.0f);
+        const float2 hv = h[q];
+        if (xa < nx) {
+            const float va = src[(long long)z * nx + xa], ha = hv.x * inv_n;
+            const float e = __fsqrt_rn(fmaf(va, va, ha * ha));
+            const float g = grad_env[fo + (long long)z * nx + xa];
+            if (e > 0.0f) {
+                const float ge = g / e;
+                re.x = ge * va;
+                im.x = ge * ha;
+            }
+        }
+        if (xa + 1 < nx) {
+            const float vb = src[(long long)z * nx + xa + 1], hb = hv.y * inv_n;
+            const float e = __fsqrt_rn(fmaf(vb, vb, hb * hb));
+            const float g = grad_env[fo + (long long)z * nx + xa + 1];
+            if (e > 0.0f) {
+                const float ge = g / e;
+                re.y = ge * vb;
+                im.y = ge * hb;
+            }
+        }
+        R[q] = re;
+        other[q] = im;
+    }
+    __syncthreads();
+    h = hilbert(other, h);
+    for (int q = threadIdx.x; q < PAIRS * n; q += blockDim.x) {
+        const int pr = q / n, z = q - pr * n;
+        const int xa = x0 + 2 * pr;
+        const float2 hv = h[q], re = R[q];
+        if (xa < nx) grad_bf[fo + (long long)z * nx + xa] = re.x - hv.x * inv_n;
+        if (xa + 1 < nx) grad_bf[fo + (long long)z * nx + xa + 1] = re.y - hv.y * inv_n;
+    }
+}
+
 }  // namespace wf
 
 using namespace wf;
@@ -158,5 +259,26 @@ extern "C" wf_status wf_envelope(const float* bf, int32_t batch, int32_t nz, int
     if (s != WF_OK) return s;
     dim3 grid((nx + 2 * kPairs - 1) / (2 * kPairs), batch);
     envelope_kernel<kPairs><<<grid, kEnvThreads, smem, st>>>(bf, env, frame_max, nz, log2n, nx);
+    return last_launch_status();
+}
+
+extern "C" wf_status wf_envelope_backward(const float* bf, int32_t batch, int32_t nz, int32_t nx,
+                                          const float* grad_env, float* grad_bf, wf_stream stream) {
+    if (!bf || !grad_env || !grad_bf || batch < 1 || batch > 65535 || nx < 1 || nz < 2 || nz > 4096)
+        return WF_ERR_INVALID_ARG;
+    if (nz & (nz - 1)) return WF_ERR_INVALID_ARG;
+    if (((uintptr_t)bf & 3u) || ((uintptr_t)grad_env & 3u) || ((uintptr_t)grad_bf & 3u))
+        return WF_ERR_INVALID_ARG;
+    int log2n = 0;
+    while ((1 << log2n) < nz) ++log2n;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    constexpr int kPairs = 1;
+    const size_t smem = sizeof(float2) * (3 * kPairs * (size_t)nz + nz / 2);
+    static unsigned long long smem_set = 0ull;
+    const size_t smem_max = sizeof(float2) * (3 * kPairs * 4096 + 2048);
+    wf_status s = ensure_smem_limit(envelope_backward_kernel<kPairs>, smem_max, smem_set);
+    if (s != WF_OK) return s;
+    dim3 grid((nx + 2 * kPairs - 1) / (2 * kPairs), batch);
+    envelope_backward_kernel<kPairs><<<grid, kEnvThreads, smem, st>>>(bf, grad_env, grad_bf, nz, log2n, nx);
     return last_launch_status();
 }

@@ -71,6 +71,106 @@ logclip_cluster_kernel(const float* env, long long frame, float lo, float hi, fl
     for (long long i = first; i < frame; i += stride) dst[i] = db_value(src[i], ref, lo, hi);
 }
 
+// Reverse mode.  Where the value is strictly inside (lo, hi) and env >
+// 1e-30 ref (same FP32 decision as the forward), d out / d env = 20 / (ln 10
+// env) and d out / d ref = -20 / (ln 10 ref); clipped, floored or NaN pixels
+// pass nothing.  When ref is the frame maximum (no caller reference, or the
+// caller says its reference is that maximum) the reference's cotangent goes to
+// the first pixel attaining it.  One 8-CTA cluster per frame: maximum (if
+// needed), then the reference cotangent and the first maximal pixel, reduced
+// in distributed shared memory in a fixed order, then the write pass.
+constexpr float kDbPerLn = 8.685889638065037f;   // 20 / ln 10
+
+__device__ __forceinline__ bool db_inside(float e, float ref, float lo, float hi) {
+    if (e != e || !(ref > 0.0f) || !(e > 1e-30f * ref)) return false;
+    const float db = 20.0f * log10f(fmaxf(e, 1e-30f * ref) / ref);
+    return db > lo && db < hi;
+}
+
+__global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kClusterThreads)
+logclip_backward_kernel(const float* env, const float* ref_in, int route, long long frame, float lo,
+                        float hi, const float* g_db, float* g_env) {
+    __shared__ float red_f[kClusterThreads / 32];
+    __shared__ long long red_i[kClusterThreads / 32];
+    __shared__ float cta_f;
+    __shared__ long long cta_i;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int b = blockIdx.y;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const float* src = env + (long long)b * frame;
+    const float* gsrc = g_db + (long long)b * frame;
+    float* dst = g_env + (long long)b * frame;
+    const long long stride = (long long)kClusterCtas * kClusterThreads;
+    const long long first = (long long)rank * kClusterThreads + threadIdx.x;
+
+    float ref;
+    if (ref_in) {
+        ref = __ldg(ref_in + b);
+    } else {
+        float m = 0.0f;
+        for (long long i = first; i < frame; i += stride) {
+            const float v = src[i];
+            if (v == v) m = fmaxf(m, v);
+        }
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) red_f[warp] = m;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float v = 0.0f;
+            for (int w = 0; w < kClusterThreads / 32; ++w) v = fmaxf(v, red_f[w]);
+            cta_f = v;
+        }
+        cluster.sync();
+        ref = 0.0f;
+        for (int r = 0; r < kClusterCtas; ++r) ref = fmaxf(ref, *cluster.map_shared_rank(&cta_f, r));
+        cluster.sync();
+    }
+    const float dref = -kDbPerLn / ref;
+    float s = 0.0f;
+    long long arg = frame;
+    if (route) {
+        for (long long i = first; i < frame; i += stride) {
+            const float e = src[i];
+            if (e == ref && i < arg) arg = i;
+            if (db_inside(e, ref, lo, hi)) s = fmaf(gsrc[i], dref, s);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            s += __shfl_xor_sync(0xffffffffu, s, o);
+            arg = min(arg, (long long)__shfl_xor_sync(0xffffffffu, arg, o));
+        }
+        if (lane == 0) {
+            red_f[warp] = s;
+            red_i[warp] = arg;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float v = 0.0f;
+            long long a = frame;
+            for (int w = 0; w < kClusterThreads / 32; ++w) {
+                v += red_f[w];
+                a = min(a, red_i[w]);
+            }
+            cta_f = v;
+            cta_i = a;
+        }
+        cluster.sync();
+        s = 0.0f;
+        arg = frame;
+        for (int r = 0; r < kClusterCtas; ++r) {
+            s += *cluster.map_shared_rank(&cta_f, r);
+            arg = min(arg, *cluster.map_shared_rank(&cta_i, r));
+        }
+        cluster.sync();
+    }
+    for (long long i = first; i < frame; i += stride) {
+        const float e = src[i];
+        float g = db_inside(e, ref, lo, hi) ? gsrc[i] * (kDbPerLn / e) : 0.0f;
+        if (i == arg) g += s;
+        dst[i] = g;
+    }
+}
+
 }  // namespace wf
 
 using namespace wf;
@@ -91,5 +191,24 @@ extern "C" wf_status wf_logclip(const float* env, int32_t batch, int32_t nz, int
         logclip_cluster_kernel<<<dim3(kClusterCtas, batch), kClusterThreads, 0, st>>>(
             env, frame, db_min, db_max, out_db);
     }
+    return last_launch_status();
+}
+
+extern "C" wf_status wf_logclip_backward(const float* env, int32_t batch, int32_t nz, int32_t nx,
+                                         const float* ref, int32_t ref_is_frame_max, float db_min,
+                                         float db_max, const float* grad_db, float* grad_env,
+                                         wf_stream stream) {
+    if (!env || !grad_db || !grad_env || batch < 1 || batch > 65535 || nz < 1 || nx < 1)
+        return WF_ERR_INVALID_ARG;
+    if (!(db_min <= db_max)) return WF_ERR_INVALID_ARG;
+    if (((uintptr_t)env & 3u) || ((uintptr_t)grad_db & 3u) || ((uintptr_t)grad_env & 3u) ||
+        ((uintptr_t)ref & 3u))
+        return WF_ERR_INVALID_ARG;
+    if (grad_env == env) return WF_ERR_INVALID_ARG;
+    const long long frame = (long long)nz * nx;
+    const int route = (!ref || ref_is_frame_max) ? 1 : 0;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    logclip_backward_kernel<<<dim3(kClusterCtas, batch), kClusterThreads, 0, st>>>(
+        env, ref, route, frame, db_min, db_max, grad_db, grad_env);
     return last_launch_status();
 }
