@@ -38,7 +38,7 @@ __host__ __device__ inline BwdSmem bwd_smem_layout(int W, int n_elements, bool n
     L.gwin = off;
     off += need_rf ? (size_t)kC * (W + 8) * sizeof(float) : 0;
     L.table = off;
-    off += (size_t)kTableStages * sizeof(StageInfo);
+    off += (size_t)kTableStages * sizeof(Stage);
     L.elems = off;
     off += (((size_t)n_elements * sizeof(Elem)) + 15) & ~(size_t)15;
     L.ge = off;
@@ -62,12 +62,13 @@ __global__ void __launch_bounds__(kThreads, 2) das_backward_kernel(const __grid_
     const BwdSmem L = bwd_smem_layout(a.W, a.g.n_elements, NEED_RF);
     float2* buf = reinterpret_cast<float2*>(smem_raw + L.pairs);   // [kC][W] (value, slope)
     float* gw = reinterpret_cast<float*>(smem_raw + L.gwin);       // [kC][W + 8] RF cotangent window
-    StageInfo* st = reinterpret_cast<StageInfo*>(smem_raw + L.table);
+    Stage* st = reinterpret_cast<Stage*>(smem_raw + L.table);      // ring of compacted stages
     Elem* el = reinterpret_cast<Elem*>(smem_raw + L.elems);        // [E range]
     float* ge = reinterpret_cast<float*>(smem_raw + L.ge);         // [E range] weight-gradient partials
     __shared__ int s_tlist[WF_MAX_TX];
     __shared__ int s_info[4];
     __shared__ float s_red[kThreads / 32];
+    __shared__ int s_cnt[kTableBatch / 32];
 
     const Geom& g = a.g;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -79,7 +80,8 @@ __global__ void __launch_bounds__(kThreads, 2) das_backward_kernel(const __grid_
     const float* rf = reinterpret_cast<const float*>(a.rf) + (long long)b * a.frame_elems;
     float* grf = NEED_RF ? a.grad_rf + (long long)b * a.frame_elems : nullptr;
     const bool vec_ok = (a.ns & 7) == 0;
-    const int GW = a.W + 8;   // cotangent window row stride
+    const int GW = a.W + 8;   // cotangent window row stride (a multiple of 8 floats)
+    const bool vec4 = NEED_RF && (a.ns & 3) == 0 && ((uintptr_t)a.grad_rf & 15u) == 0;
     const long long E = g.n_elements;
 
     const int col = WCOL * warp + lx;
@@ -134,43 +136,16 @@ __global__ void __launch_bounds__(kThreads, 2) das_backward_kernel(const __grid_
     const int n_act = s_info[0], k_a = s_info[1], k_b = s_info[2], q0 = s_info[3];
     const int n_stages = n_e == 0 ? 0 : SYM ? sym_prefix(k_b, nc, n_e) - q0 : (k_b - k_a) * n_act;
 
-    auto locate = [&](int q, int& k, int& j) {
-        if (SYM) {
-            const int qg = q0 + q;
-            k = sym_chunk(qg, nc);
-            j = qg - 4 * k * (k + 1);
-        } else {
-            k = k_a + q / n_act;
-            j = q - (q / n_act) * n_act;
+    const StageSpace sp{er, n_e, nc, n_act, k_a, q0, n_stages, s_tlist};
+    auto tx_of = [&](int j) { return stage_tx<SYM>(sp, j); };
+    int n_live = 0, raw_next = 0;
+    auto need = [&](int upto) {   // make entry `upto` exist while raw stages are left
+        while (n_live <= upto && raw_next < n_stages) {
+            n_live += fill_stages<MODE, SYM>(a, tg, el, sp, st, s_cnt, raw_next, n_live);
+            raw_next += kTableBatch;
         }
     };
-    auto tx_of = [&](int j) { return SYM ? er.x + j : s_tlist[j]; };
-    auto advance = [&](int& k, int& j) {
-        if (++j == (SYM ? min(kC * (k + 1), n_e) : n_act)) {
-            j = 0;
-            ++k;
-        }
-    };
-    auto fill_table = [&](int base) {
-        const int q = base + tid;
-        if (tid < kTableBatch && q < n_stages) {
-            int k, j;
-            locate(q, k, j);
-            const int t = tx_of(j);
-            const int rr0 = er.x + k * kC, rrl = min(rr0 + kC - 1, er.y);
-            const TxInfo& ti = a.tx[t];
-            float mn = 3.0e38f, mx = -3.0e38f;
-            for (int rr = SYM ? max(rr0, t) : rr0; rr <= rrl; ++rr) {
-                const float2 bd = pair_bounds<MODE>(g, ti, rr, tg.xlo, tg.xhi, tg.zlo, tg.zhi);
-                mn = fminf(mn, bd.x);
-                mx = fmaxf(mx, bd.y);
-            }
-            const DF txref = tx_ref<MODE>(ti, tg.cx, tg.cz,
-                                          MODE == 0 ? elem_R(el[ti.e - er.x]) : DF{0.0f, 0.0f});
-            st[q & (kTableStages - 1)] = make_stage(a, mn, mx, txref, elem_R(el[rr0 - er.x]));
-        }
-    };
-    fill_table(0);
+    need(0);
 
     float Dr[kC][P], Wr[kC][P], Ar[kC][P], gR[kC];
     float dr_min = 0.0f, dr_max = 0.0f, accC = 0.0f;
@@ -187,33 +162,29 @@ __global__ void __launch_bounds__(kThreads, 2) das_backward_kernel(const __grid_
         }
     };
 
-    int k = k_a, j = 0;
-    int k1 = k_a, j1 = 0;
-    __syncthreads();
-    if (n_stages > 0) {
-        advance(k1, j1);
-        const StageInfo s0 = st[0];
-        const int rr0 = er.x + k_a * kC;
-        if (!s0.skip()) stage_prefetch<float, SYM>(rs, a, rf, s0, tx_of(0), rr0, min(rr0 + kC - 1, er.y), vec_ok);
+    if (n_live > 0) {
+        const Stage s0 = st[0];
+        const int rr0 = er.x + s0.k() * kC;
+        stage_prefetch<float, SYM>(rs, a, rf, s0, tx_of(s0.j()), rr0, min(rr0 + kC - 1, er.y), vec_ok);
     }
-    for (int q = 0; q < n_stages; ++q) {
+    int k_cur = -1;
+    for (int q = 0; q < n_live; ++q) {
+        const Stage si = st[q & (kTableStages - 1)];
+        const int k = si.k();
         const int r0 = er.x + k * kC;
         const int r_last = min(r0 + kC - 1, er.y);
-        const int t = tx_of(j);
-        const StageInfo si = st[q & (kTableStages - 1)];
-        if (!si.skip()) stage_store<float, SYM>(rs, buf, a, si, t, r0, r_last);
+        const int t = tx_of(si.j());
+        stage_store<float, SYM>(rs, buf, a, si, t, r0, r_last);
         __syncthreads();   // pairs of stage q visible; cotangent window zero
-        if (q + 1 < n_stages) {
-            if (((q + 1) & (kTableBatch - 1)) == 0) {
-                fill_table(q + 1);
-                __syncthreads();
-            }
-            const StageInfo s1 = st[(q + 1) & (kTableStages - 1)];
-            const int rr0 = er.x + k1 * kC;
-            if (!s1.skip()) stage_prefetch<float, SYM>(rs, a, rf, s1, tx_of(j1), rr0, min(rr0 + kC - 1, er.y), vec_ok);
+        need(q + 1);
+        if (q + 1 < n_live) {
+            const Stage s1 = st[(q + 1) & (kTableStages - 1)];
+            const int rr0 = er.x + s1.k() * kC;
+            stage_prefetch<float, SYM>(rs, a, rf, s1, tx_of(s1.j()), rr0, min(rr0 + kC - 1, er.y), vec_ok);
         }
-        if (j == 0) {
-            if (q > 0) flush_chunk(r0 - kC);
+        if (k != k_cur) {
+            if (k_cur >= 0) flush_chunk(er.x + k_cur * kC);
+            k_cur = k;
             cmask = 0u;
 #pragma unroll
             for (int c = 0; c < kC; ++c) {
@@ -245,7 +216,7 @@ __global__ void __launch_bounds__(kThreads, 2) das_backward_kernel(const __grid_
         }
         unsigned cm = cmask;
         if (SYM && t > r0) cm &= ~((1u << (t - r0)) - 1u);
-        bool live = !si.skip() && cm != 0u;
+        bool live = cm != 0u;
         if (MODE == 0) live = live && a.tx[t].e >= wr.x && a.tx[t].e <= wr.y;
         float tw[P], yt[P], ya[P];
         if (live) {
@@ -314,30 +285,41 @@ __global__ void __launch_bounds__(kThreads, 2) das_backward_kernel(const __grid_
         }
         if (NEED_RF) {
             __syncthreads();   // every contribution of stage q is in the window; pairs no longer read
-            if (!si.skip()) {
-                // window position n covers samples lo + n, n in [0, len]; rows paired with t
-                const int span = si.len + 1, nrow = r_last - r0 + 1;
-                for (int i = tid; i < nrow * span; i += kThreads) {
-                    const int c = i / span, n = i - c * span;
-                    float* cell = gw + c * GW + n;
-                    const float v = *cell;
-                    if (v == 0.0f) continue;
-                    *cell = 0.0f;
-                    const int smp = si.lo + n;
-                    if (smp < 0 || smp >= a.ns) continue;
-                    atomicAdd(grf + ((long long)t * E + r0 + c) * a.ns + smp, v);
-                    if (SYM && r0 + c > t) atomicAdd(grf + ((long long)(r0 + c) * E + t) * a.ns + smp, v);
+            {
+                // window positions n = 4 m .. 4 m + 3 cover samples lo + n (lo is a multiple of
+                // 8, contributions reach n <= len); rows paired with t.  Whole groups inside
+                // the record go out as one 16-byte atomic add, edge groups sample by sample.
+                const int span4 = (si.len + 4) >> 2, nrow = r_last - r0 + 1;
+                for (int i = tid; i < nrow * span4; i += kThreads) {
+                    const int c = i / span4, m = i - c * span4;
+                    float4* cell = reinterpret_cast<float4*>(gw + c * GW + 4 * m);
+                    const float4 v = *cell;
+                    if (v.x == 0.0f && v.y == 0.0f && v.z == 0.0f && v.w == 0.0f) continue;
+                    *cell = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                    const int smp = si.lo + 4 * m;
+                    const bool mirror = SYM && r0 + c > t;
+                    float* d0 = grf + ((long long)t * E + r0 + c) * a.ns + smp;
+                    float* d1 = mirror ? grf + ((long long)(r0 + c) * E + t) * a.ns + smp : d0;
+                    if (vec4 && smp >= 0 && smp + 4 <= a.ns) {
+                        atomicAdd(reinterpret_cast<float4*>(d0), v);
+                        if (mirror) atomicAdd(reinterpret_cast<float4*>(d1), v);
+                    } else {
+                        const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            if (vv[u] == 0.0f || smp + u < 0 || smp + u >= a.ns) continue;
+                            atomicAdd(d0 + u, vv[u]);
+                            if (mirror) atomicAdd(d1 + u, vv[u]);
+                        }
+                    }
                 }
             }
         } else {
             __syncthreads();   // pairs no longer read
         }
-        k = k1;
-        j = j1;
-        advance(k1, j1);
     }
     if (NEED_PAR) {
-        if (n_stages > 0) flush_chunk(er.x + (k_b - 1) * kC);   // the CTA's last chunk
+        if (k_cur >= 0) flush_chunk(er.x + k_cur * kC);   // the CTA's last chunk
         const float sc = warp_sum(accC);
         if (lane == 0) s_red[warp] = sc;
         __syncthreads();

@@ -257,6 +257,24 @@ __device__ __forceinline__ StageInfo make_stage(const DasArgs& a, float mn, floa
     return si;
 }
 
+// A stage of a CTA's compacted list (only windows that reach the record): its
+// window and its place in the (receive chunk k, transmit slot j) order.
+struct Stage {
+    int lo, len;
+    float B;
+    int meta;   // bit 0: window crosses an end of the record; bit 1: clamped over-long
+                // window; bits 2..11: receive chunk k; bits 12..31: transmit slot j
+    __device__ __forceinline__ bool edge() const { return meta & 1; }
+    __device__ __forceinline__ bool over() const { return (meta >> 1) & 1; }
+    __device__ __forceinline__ int k() const { return (meta >> 2) & 1023; }
+    __device__ __forceinline__ int j() const { return (int)((unsigned)meta >> 12); }
+};
+
+__device__ __forceinline__ Stage pack_stage(const StageInfo& si, int k, int j) {
+    return Stage{si.lo, si.len, si.B,
+                 (si.edge() ? 1 : 0) | (si.over() ? 2 : 0) | (k << 2) | (j << 12)};
+}
+
 // Reciprocal STAI stage bookkeeping.  With n_e elements in the tile's range
 // and nc = ceil(n_e / 8) receive chunks, chunk k pairs with the transmits
 // er.x .. er.x + min(8 (k + 1), n_e) - 1 (those not after its last element).
@@ -480,7 +498,7 @@ __host__ __device__ inline SmemLayout smem_layout(int W, int n_elements, bool db
     L.pairs = off;
     off += (size_t)(db ? 2 : 1) * kC * W * sizeof(float2);
     L.table = off;
-    off += (size_t)kTableStages * sizeof(StageInfo);
+    off += (size_t)kTableStages * sizeof(Stage);
     L.elems = off;
     off += (((size_t)n_elements * sizeof(Elem)) + 15) & ~(size_t)15;
     L.raw = off;
@@ -498,7 +516,7 @@ struct RegStage {
 
 template <typename T, bool SYM>
 __device__ __forceinline__ void stage_prefetch(RegStage<T, SYM>& rs, const DasArgs& a, const T* rf,
-                                               const StageInfo& si, int t, int r0, int r_last,
+                                               const Stage& si, int t, int r0, int r_last,
                                                bool vec_ok) {
     const int nseg = si.len >> 3;
     const int k = threadIdx.x & 63;
@@ -516,7 +534,7 @@ __device__ __forceinline__ void stage_prefetch(RegStage<T, SYM>& rs, const DasAr
 
 template <typename T, bool SYM>
 __device__ __forceinline__ void stage_store(const RegStage<T, SYM>& rs, float2* buf, const DasArgs& a,
-                                            const StageInfo& si, int t, int r0, int r_last) {
+                                            const Stage& si, int t, int r0, int r_last) {
     const int nseg = si.len >> 3;
     const int k = threadIdx.x & 63;
 #pragma unroll
@@ -531,6 +549,77 @@ __device__ __forceinline__ void stage_store(const RegStage<T, SYM>& rs, float2* 
     }
 }
 
+// A CTA's stage space: receive chunks [k_a, k_b) of the tile's element range
+// er, chunk-outer, with every active transmit per chunk (reciprocal STAI:
+// transmits up to the chunk's last element).  Raw stage q maps to (chunk k,
+// transmit slot j); slot j is transmit tlist[j], or er.x + j when reciprocal.
+struct StageSpace {
+    int2 er;
+    int n_e, nc, n_act, k_a, q0, n_stages;
+    const int* tlist;
+};
+
+template <bool SYM>
+__device__ __forceinline__ void locate_stage(const StageSpace& sp, int q, int& k, int& j) {
+    if (SYM) {
+        const int qg = sp.q0 + q;
+        k = sym_chunk(qg, sp.nc);
+        j = qg - 4 * k * (k + 1);
+    } else {
+        k = sp.k_a + q / sp.n_act;
+        j = q - (q / sp.n_act) * sp.n_act;
+    }
+}
+
+template <bool SYM>
+__device__ __forceinline__ int stage_tx(const StageSpace& sp, int j) {
+    return SYM ? sp.er.x + j : sp.tlist[j];
+}
+
+// Scan raw stages [base, base + kTableBatch) of the stage space: the windows
+// that reach the record are appended in order to the ring `st` at position
+// `live`.  Called by every thread of the CTA (two barriers); returns the number
+// appended (block-uniform).  s_cnt: kTableBatch / 32 ints of shared scratch.
+template <int MODE, bool SYM>
+__device__ __forceinline__ int fill_stages(const DasArgs& a, const TileGeo& tg, const Elem* el,
+                                           const StageSpace& sp, Stage* st, int* s_cnt, int base,
+                                           int live) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int q = base + tid;
+    bool keep = false;
+    Stage e{};
+    if (tid < kTableBatch && q < sp.n_stages) {
+        int k, j;
+        locate_stage<SYM>(sp, q, k, j);
+        const int t = stage_tx<SYM>(sp, j);
+        const int rr0 = sp.er.x + k * kC, rrl = min(rr0 + kC - 1, sp.er.y);
+        const TxInfo& ti = a.tx[t];
+        float mn = 3.0e38f, mx = -3.0e38f;
+        for (int rr = SYM ? max(rr0, t) : rr0; rr <= rrl; ++rr) {
+            const float2 bd = pair_bounds<MODE>(a.g, ti, rr, tg.xlo, tg.xhi, tg.zlo, tg.zhi);
+            mn = fminf(mn, bd.x);
+            mx = fmaxf(mx, bd.y);
+        }
+        const DF txref = tx_ref<MODE>(ti, tg.cx, tg.cz,
+                                      MODE == 0 ? elem_R(el[ti.e - sp.er.x]) : DF{0.0f, 0.0f});
+        const StageInfo si = make_stage(a, mn, mx, txref, elem_R(el[rr0 - sp.er.x]));
+        keep = !si.skip();
+        e = pack_stage(si, k, j);
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+    if (lane == 0 && warp < kTableBatch / 32) s_cnt[warp] = __popc(bal);
+    __syncthreads();
+    int off = __popc(bal & ((1u << lane) - 1u)), total = 0;
+#pragma unroll
+    for (int w = 0; w < kTableBatch / 32; ++w) {
+        if (w < warp) off += s_cnt[w];
+        total += s_cnt[w];
+    }
+    if (keep) st[(live + off) & (kTableStages - 1)] = e;
+    __syncthreads();
+    return total;
+}
+
 template <int MODE, typename T, int WCOL, int P, bool DB, bool TMA, bool CHECK, bool SYM>
 __global__ void __launch_bounds__(kThreads, 2) das_tiled_kernel(const __grid_constant__ DasArgs a) {
     static_assert(!SYM || MODE == 0, "reciprocal pairing is an STAI property");
@@ -539,12 +628,13 @@ __global__ void __launch_bounds__(kThreads, 2) das_tiled_kernel(const __grid_con
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const SmemLayout L = smem_layout(a.W, a.g.n_elements, DB, TMA, SYM, a.ring, (int)sizeof(T));
     float2* buf0 = reinterpret_cast<float2*>(smem_raw + L.pairs);   // [DB+1][kC][W] pairs
-    StageInfo* st = reinterpret_cast<StageInfo*>(smem_raw + L.table);
+    Stage* st = reinterpret_cast<Stage*>(smem_raw + L.table);        // ring of compacted stages
     Elem* el = reinterpret_cast<Elem*>(smem_raw + L.elems);         // [E range]
     T* raw = reinterpret_cast<T*>(smem_raw + L.raw);                // [ring][kRawRows][W + 8]
     __shared__ __align__(8) unsigned long long s_bar[kMaxRing];
     __shared__ int s_tlist[WF_MAX_TX];
     __shared__ int s_info[4];
+    __shared__ int s_cnt[kTableBatch / 32];
 
     const Geom& g = a.g;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -610,76 +700,45 @@ __global__ void __launch_bounds__(kThreads, 2) das_tiled_kernel(const __grid_con
     const int n_act = s_info[0], k_a = s_info[1], k_b = s_info[2], q0 = s_info[3];
     const int n_stages = n_e == 0 ? 0 : SYM ? sym_prefix(k_b, nc, n_e) - q0 : (k_b - k_a) * n_act;
 
-    // Stage q -> (receive chunk k, transmit slot j); transmit index of slot j.
-    auto locate = [&](int q, int& k, int& j) {
-        if (SYM) {
-            const int qg = q0 + q;
-            k = sym_chunk(qg, nc);
-            j = qg - 4 * k * (k + 1);
-        } else {
-            k = k_a + q / n_act;
-            j = q - (q / n_act) * n_act;
+    const StageSpace sp{er, n_e, nc, n_act, k_a, q0, n_stages, s_tlist};
+    auto tx_of = [&](int j) { return stage_tx<SYM>(sp, j); };
+    int n_live = 0, raw_next = 0;
+    // Make entry `upto` of the compacted list exist while raw stages are left (all threads).
+    auto need = [&](int upto) {
+        while (n_live <= upto && raw_next < n_stages) {
+            n_live += fill_stages<MODE, SYM>(a, tg, el, sp, st, s_cnt, raw_next, n_live);
+            raw_next += kTableBatch;
         }
     };
-    auto tx_of = [&](int j) { return SYM ? er.x + j : s_tlist[j]; };
-    auto advance = [&](int& k, int& j) {
-        if (++j == (SYM ? min(kC * (k + 1), n_e) : n_act)) {
-            j = 0;
-            ++k;
-        }
-    };
-
-    // Stage windows, kTableBatch at a time into a ring of kTableStages.
-    auto fill_table = [&](int base) {
-        const int q = base + tid;
-        if (tid < kTableBatch && q < n_stages) {
-            int k, j;
-            locate(q, k, j);
-            const int t = tx_of(j);
-            const int rr0 = er.x + k * kC, rrl = min(rr0 + kC - 1, er.y);
-            const TxInfo& ti = a.tx[t];
-            float mn = 3.0e38f, mx = -3.0e38f;
-            for (int rr = SYM ? max(rr0, t) : rr0; rr <= rrl; ++rr) {
-                const float2 bd = pair_bounds<MODE>(g, ti, rr, tg.xlo, tg.xhi, tg.zlo, tg.zhi);
-                mn = fminf(mn, bd.x);
-                mx = fmaxf(mx, bd.y);
-            }
-            const DF txref = tx_ref<MODE>(ti, tg.cx, tg.cz,
-                                          MODE == 0 ? elem_R(el[ti.e - er.x]) : DF{0.0f, 0.0f});
-            st[q & (kTableStages - 1)] = make_stage(a, mn, mx, txref, elem_R(el[rr0 - er.x]));
-        }
-    };
-    // TMA producer (thread 0): raw windows of stage qq into ring slot qq % ring.
+    // TMA producer (warp 0): raw windows of entry qq into ring slot qq % ring.  Lane 0
+    // posts the byte count, then lane c copies chunk row c (lanes 8 + c: mirrored rows).
     auto issue = [&](int qq) {
-        const StageInfo si = st[qq & (kTableStages - 1)];
+        const Stage si = st[qq & (kTableStages - 1)];
         unsigned long long* bar = &s_bar[qq % ring];
-        int k, j;
-        locate(qq, k, j);
-        const int t = tx_of(j);
-        const int rr0 = er.x + k * kC, nrow = min(rr0 + kC - 1, er.y) - rr0 + 1;
+        const int t = tx_of(si.j());
+        const int rr0 = er.x + si.k() * kC, nrow = min(rr0 + kC - 1, er.y) - rr0 + 1;
         const int na = max(si.lo, 0), nb = min(si.lo + si.len + 8, a.ns);
-        if (si.skip() || nb <= na) {
-            mbar_arrive_expect(bar, 0u);
-            return;
-        }
-        const int ca = SYM ? max(t - rr0, 0) : 0;       // first chunk row paired with t
-        const int cb = SYM ? max(t - rr0 + 1, 0) : nrow; // first row with a mirrored trace
-        const unsigned bytes = (unsigned)((nb - na) * (int)sizeof(T));
-        fence_async_shared();
-        mbar_arrive_expect(bar, bytes * (unsigned)((nrow - ca) + (nrow - cb)));
+        const int ca = SYM ? max(t - rr0, 0) : 0;        // first chunk row paired with t
+        const int cb = SYM ? max(t - rr0 + 1, 0) : nrow;  // first row with a mirrored trace
+        const unsigned bytes = nb > na ? (unsigned)((nb - na) * (int)sizeof(T)) : 0u;
+        if (lane == 0) mbar_arrive_expect(bar, bytes * (unsigned)((nrow - ca) + (nrow - cb)));
+        __syncwarp();
+        if (bytes == 0u) return;
         T* slot = raw + (size_t)(qq % ring) * kRawRows * RW;
         const long long E = g.n_elements;
-        const T* src = rf + ((long long)t * E + rr0) * a.ns + na;   // trace (t, rr0 + c)
-        for (int c = ca; c < nrow; ++c)
-            bulk_copy_g2s(slot + c * RW + (na - si.lo), src + (long long)c * a.ns, bytes, bar);
-        if (SYM) {
-            const T* srcb = rf + ((long long)rr0 * E + t) * a.ns + na;   // trace (rr0 + c, t)
-            for (int c = cb; c < nrow; ++c)
-                bulk_copy_g2s(slot + (kC + c) * RW + (na - si.lo), srcb + (long long)c * E * a.ns, bytes, bar);
+        const int c = lane & (kC - 1);
+        if (lane < kC && c >= ca && c < nrow) {
+            fence_async_shared();
+            bulk_copy_g2s(slot + c * RW + (na - si.lo), rf + ((long long)t * E + rr0 + c) * a.ns + na,
+                          bytes, bar);
+        } else if (SYM && lane >= kC && lane < 2 * kC && c >= cb && c < nrow) {
+            fence_async_shared();
+            bulk_copy_g2s(slot + (kC + c) * RW + (na - si.lo),
+                          rf + ((long long)(rr0 + c) * E + t) * a.ns + na, bytes, bar);
         }
     };
     const int ahead = TMA ? ring - 1 : 1;   // stages in flight ahead of the one being converted
-    fill_table(0);
+    need(ahead - 1);
 
     // PWI: range of the transmit correction ux sin + uz cos over this warp's pixels.
     const float wux0 = (float)(WCOL * warp) * g.gdx, wux1 = (float)(WCOL * warp + WCOL - 1) * g.gdx;
@@ -693,32 +752,28 @@ __global__ void __launch_bounds__(kThreads, 2) das_tiled_kernel(const __grid_con
     unsigned cmask = 0u;
     RegStage<T, SYM> rs;
 
-    int k = k_a, j = 0;     // stage q
-    int k1 = k_a, j1 = 0;   // stage q + 1 (register path)
-    __syncthreads();
-    if (n_stages > 0) {
-        advance(k1, j1);
-        if (TMA) {
-            if (tid == 0)
-                for (int qq = 0; qq < min(ahead, n_stages); ++qq) issue(qq);
-        } else {
-            const StageInfo s0 = st[0];
-            const int rr0 = er.x + k_a * kC;
-            if (!s0.skip()) stage_prefetch<T, SYM>(rs, a, rf, s0, tx_of(0), rr0, min(rr0 + kC - 1, er.y), vec_ok);
-        }
+    if (TMA) {
+        if (warp == 0)
+            for (int qq = 0; qq < min(ahead, n_live); ++qq) issue(qq);
+    } else if (n_live > 0) {
+        const Stage s0 = st[0];
+        const int rr0 = er.x + s0.k() * kC;
+        stage_prefetch<T, SYM>(rs, a, rf, s0, tx_of(s0.j()), rr0, min(rr0 + kC - 1, er.y), vec_ok);
     }
 
-    for (int q = 0; q < n_stages; ++q) {
+    int k_cur = -1;
+    for (int q = 0; q < n_live; ++q) {
+        const Stage si = st[q & (kTableStages - 1)];
+        const int k = si.k();
         const int r0 = er.x + k * kC;
         const int r_last = min(r0 + kC - 1, er.y);
-        const int t = tx_of(j);
-        const StageInfo si = st[q & (kTableStages - 1)];
+        const int t = tx_of(si.j());
         float2* buf = buf0 + (DB ? (q & 1) * kC * a.W : 0);
-        if (si.over() && tid == 0) flag(a.hdr, 1u, (unsigned)blockIdx.x, (unsigned)si.over(), (unsigned)a.W);
+        if (si.over() && tid == 0) flag(a.hdr, 1u, (unsigned)blockIdx.x, (unsigned)si.len, (unsigned)a.W);
         bool stuck = false;
         if (TMA) {
             stuck = !mbar_wait_bounded(&s_bar[q % ring], (unsigned)((q / ring) & 1));
-            if (!stuck && !si.skip()) {
+            if (!stuck) {
                 // raw slot -> FP32 pairs, segment (trace c, block kk) = (tid >> 6 [+4], tid & 63)
                 const T* slot = raw + (size_t)(q % ring) * kRawRows * RW;
                 const int nseg = si.len >> 3, kk = tid & 63;
@@ -743,7 +798,7 @@ __global__ void __launch_bounds__(kThreads, 2) das_tiled_kernel(const __grid_con
                     }
                 }
             }
-        } else if (!si.skip()) {
+        } else {
             stage_store<T, SYM>(rs, buf, a, si, t, r0, r_last);
         }
         // pairs of stage q visible; raw slot of stage q - 1 and (double-buffered) pairs of q - 1 free
@@ -752,25 +807,23 @@ __global__ void __launch_bounds__(kThreads, 2) das_tiled_kernel(const __grid_con
             // (bounded), and leave the stage loop together.
             if (tid == 0) {
                 flag(a.hdr, 4u, (unsigned)blockIdx.x, (unsigned)q, 0u);
-                for (int qq = q + 1; qq < min(q + ahead, n_stages); ++qq)
+                for (int qq = q + 1; qq < min(q + ahead, n_live); ++qq)
                     mbar_wait_bounded(&s_bar[qq % ring], (unsigned)((qq / ring) & 1));
             }
             break;
         }
-        if (q + ahead < n_stages) {
-            if (((q + ahead) & (kTableBatch - 1)) == 0) {
-                fill_table(q + ahead);
-                __syncthreads();
-            }
+        need(q + ahead);
+        if (q + ahead < n_live) {
             if (TMA) {
-                if (tid == 0) issue(q + ahead);
+                if (warp == 0) issue(q + ahead);
             } else {
-                const StageInfo s1 = st[(q + 1) & (kTableStages - 1)];
-                const int rr0 = er.x + k1 * kC;
-                if (!s1.skip()) stage_prefetch<T, SYM>(rs, a, rf, s1, tx_of(j1), rr0, min(rr0 + kC - 1, er.y), vec_ok);
+                const Stage s1 = st[(q + 1) & (kTableStages - 1)];
+                const int rr0 = er.x + s1.k() * kC;
+                stage_prefetch<T, SYM>(rs, a, rf, s1, tx_of(s1.j()), rr0, min(rr0 + kC - 1, er.y), vec_ok);
             }
         }
-        if (j == 0) {
+        if (k != k_cur) {
+            k_cur = k;
             // New receive chunk: which elements weigh on this warp, and (only for those)
             // window-relative distances C_c + delta and weights (times the int16 scale).
             cmask = 0u;
@@ -804,7 +857,7 @@ __global__ void __launch_bounds__(kThreads, 2) das_tiled_kernel(const __grid_con
         // an end of the record).
         unsigned cm = cmask;
         if (SYM && t > r0) cm &= ~((1u << (t - r0)) - 1u);   // pairs below the diagonal
-        bool live = !si.skip() && cm != 0u;
+        bool live = cm != 0u;
         if (MODE == 0) live = live && a.tx[t].e >= wr.x && a.tx[t].e <= wr.y;
         float tw[P], wt[P];
         if (live) {
@@ -865,9 +918,6 @@ __global__ void __launch_bounds__(kThreads, 2) das_tiled_kernel(const __grid_con
             for (int p = 0; p < P; ++p) acc[p] = MODE == 0 ? fmaf(wt[p], acct[p], acc[p]) : acc[p] + acct[p];
         }
         if (!DB) __syncthreads();   // single buffer: compute of stage q done before stage q + 1 lands
-        k = k1;
-        j = j1;
-        advance(k1, j1);
     }
 
     // Partial tile in thread order: [p][tid].
