@@ -213,19 +213,31 @@ Plan plan_for(int mode, const Cfg& cfg, const GeomD& D, const wf_probe* p, const
     // WF_DAS_NO_TMA=1 selects the register-staged path instead (tuning and testing).
     const char* no_tma = std::getenv("WF_DAS_NO_TMA");
     P.tma = ns % 8 == 0 && !(no_tma && no_tma[0] && no_tma[0] != '0');
+    // Deepest TMA ring (stages in flight) that fits two CTAs per SM, double-buffered pairs
+    // preferred; WF_DAS_RING=n caps the depth (tuning).
     bool found = false;
-    const int rings[2] = {P.tma ? 3 : 1, P.tma ? 2 : 1};
-    for (int ri = 0; ri < 2 && !found; ++ri)
-        for (int dbi = 0; dbi < 2 && !found; ++dbi) {
-            const bool db = dbi == 0 && P.tma;
-            const SmemLayout L = smem_layout(P.W, p->n_elements, db, P.tma, P.sym, rings[ri], rf_bytes);
-            if (L.total <= kSmemBudget) {
-                P.ring = rings[ri];
-                P.db = db;
-                P.smem = L.total;
-                found = true;
-            }
+    int max_ring = kMaxRing;
+    if (const char* r = std::getenv("WF_DAS_RING")) max_ring = std::max(2, std::min(kMaxRing, std::atoi(r)));
+    struct Cand { bool db; int ring; };
+    Cand cands[2 * kMaxRing + 2];
+    int nc = 0;
+    if (P.tma) {
+        for (int r = max_ring; r >= 3; --r) cands[nc++] = {true, r};
+        for (int r = max_ring; r >= 3; --r) cands[nc++] = {false, r};
+        cands[nc++] = {true, 2};
+        cands[nc++] = {false, 2};
+    } else {
+        cands[nc++] = {false, 1};
+    }
+    for (int i = 0; i < nc && !found; ++i) {
+        const SmemLayout L = smem_layout(P.W, p->n_elements, cands[i].db, P.tma, P.sym, cands[i].ring, rf_bytes);
+        if (L.total <= kSmemBudget) {
+            P.ring = cands[i].ring;
+            P.db = cands[i].db;
+            P.smem = L.total;
+            found = true;
         }
+    }
     if (!found) {
         P.ring = P.tma ? 2 : 1;
         P.db = false;

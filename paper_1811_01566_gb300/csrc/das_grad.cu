@@ -61,13 +61,14 @@ __global__ void __launch_bounds__(kThreads, 2) das_backward_kernel(const __grid_
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const BwdSmem L = bwd_smem_layout(a.W, a.g.n_elements, NEED_RF);
     float2* buf = reinterpret_cast<float2*>(smem_raw + L.pairs);   // [kC][W] (value, slope)
-    float* gw = reinterpret_cast<float*>(smem_raw + L.gwin);       // [kC][W + 8] RF cotangent window
+    int* gw = reinterpret_cast<int*>(smem_raw + L.gwin);           // [kC][W + 8] RF cotangent window (fixed point)
     Stage* st = reinterpret_cast<Stage*>(smem_raw + L.table);      // ring of compacted stages
     Elem* el = reinterpret_cast<Elem*>(smem_raw + L.elems);        // [E range]
     float* ge = reinterpret_cast<float*>(smem_raw + L.ge);         // [E range] weight-gradient partials
     __shared__ int s_tlist[WF_MAX_TX];
     __shared__ int s_info[4];
     __shared__ float s_red[kThreads / 32];
+    __shared__ float s_gm[kThreads / 32];
     __shared__ int s_cnt[kTableBatch / 32];
 
     const Geom& g = a.g;
@@ -101,12 +102,45 @@ __global__ void __launch_bounds__(kThreads, 2) das_backward_kernel(const __grid_
     const int2 er = tg.er;
     const int n_e = er.y >= er.x ? er.y - er.x + 1 : 0;
     const int nc = (n_e + kC - 1) / kC;
+    float gmax = 0.0f;
     for (int e = er.x + tid; e <= er.y; e += kThreads) {
         el[e - er.x] = make_elem(a, tg.cx, tg.cz, e);
         ge[e - er.x] = 0.0f;
+        gmax = fmaxf(gmax, fabsf(el[e - er.x].g));
     }
     if (NEED_RF)
-        for (int i = tid; i < kC * GW; i += kThreads) gw[i] = 0.0f;
+        for (int i = tid; i < kC * GW; i += kThreads) gw[i] = 0;
+    // Fixed-point scale of the RF cotangent window.  A contribution is y W times
+    // (1 - f) or f, |y W| <= ymax wmax (windows <= 1), and one window position
+    // collects at most one unit-weight share per pixel of the tile, so with
+    // scale = 2^21 / (ymax wmax) every contribution rounds exactly through the
+    // 1.5 * 2^23 add and no 32-bit sum can overflow (256 P pixels <= 2^9).
+    // Shared-memory integer atomics run about three times the rate of float ones.
+    float scale = 0.0f, inv_scale = 0.0f;
+    if (NEED_RF) {
+        float ym = 0.0f;
+#pragma unroll
+        for (int p = 0; p < P; ++p) ym = fmaxf(ym, fabsf(y[p]));
+        ym = warp_max(ym);
+        const float gm = warp_max(gmax);
+        if (lane == 0) {
+            s_red[warp] = ym;
+            s_gm[warp] = gm;
+        }
+        __syncthreads();
+        float ymax = 0.0f, wmax = 0.0f;
+        for (int w = 0; w < kThreads / 32; ++w) {
+            ymax = fmaxf(ymax, s_red[w]);
+            wmax = fmaxf(wmax, s_gm[w]);
+        }
+        if (MODE == 0) wmax *= wmax;   // transmit and receive weights
+        const float m = ymax * wmax;
+        if (m > 0.0f && m < 3.0e38f) {
+            scale = 2097152.0f / m;
+            inv_scale = m * (1.0f / 2097152.0f);
+        }
+        static_assert(kThreads * P <= 512, "fixed-point headroom assumes at most 512 pixels per tile");
+    }
     if (tid == 0) {
         int n = 0;
         if (!SYM && n_e > 0)
@@ -256,7 +290,7 @@ __global__ void __launch_bounds__(kThreads, 2) das_backward_kernel(const __grid_
             for (int c = 0; c < kC; ++c) {
                 if (!((cm >> c) & 1u)) continue;
                 const float2* bc = buf + c * a.W;
-                float* gc = gw + c * GW;
+                int* gc = gw + c * GW;
 #pragma unroll
                 for (int p = 0; p < P; ++p) {
                     const float s = tw[p] + Dr[c][p];
@@ -268,8 +302,9 @@ __global__ void __launch_bounds__(kThreads, 2) das_backward_kernel(const __grid_
                     const bool ok = (unsigned)(si.lo + idx) <= (unsigned)(a.ns - 2);
                     const float yW = ok ? yt[p] * Wr[c][p] : 0.0f;
                     if (NEED_RF && yW != 0.0f) {
-                        atomicAdd(gc + idx, yW - yW * f);
-                        atomicAdd(gc + idx + 1, yW * f);
+                        const float w1 = yW * f;
+                        atomicAdd(gc + idx, __float_as_int(fmaf(yW - w1, scale, kMagic)) - kMagicBits);
+                        atomicAdd(gc + idx + 1, __float_as_int(fmaf(w1, scale, kMagic)) - kMagicBits);
                     }
                     if (NEED_PAR) {
                         accC = fmaf(yW * ab.y, base_c + s, accC);
@@ -292,10 +327,12 @@ __global__ void __launch_bounds__(kThreads, 2) das_backward_kernel(const __grid_
                 const int span4 = (si.len + 4) >> 2, nrow = r_last - r0 + 1;
                 for (int i = tid; i < nrow * span4; i += kThreads) {
                     const int c = i / span4, m = i - c * span4;
-                    float4* cell = reinterpret_cast<float4*>(gw + c * GW + 4 * m);
-                    const float4 v = *cell;
-                    if (v.x == 0.0f && v.y == 0.0f && v.z == 0.0f && v.w == 0.0f) continue;
-                    *cell = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                    int4* cell = reinterpret_cast<int4*>(gw + c * GW + 4 * m);
+                    const int4 qv = *cell;
+                    if ((qv.x | qv.y | qv.z | qv.w) == 0) continue;
+                    *cell = make_int4(0, 0, 0, 0);
+                    const float4 v = make_float4((float)qv.x * inv_scale, (float)qv.y * inv_scale,
+                                                 (float)qv.z * inv_scale, (float)qv.w * inv_scale);
                     const int smp = si.lo + 4 * m;
                     const bool mirror = SYM && r0 + c > t;
                     float* d0 = grf + ((long long)t * E + r0 + c) * a.ns + smp;

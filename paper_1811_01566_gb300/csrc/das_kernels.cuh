@@ -484,7 +484,7 @@ __device__ __forceinline__ float warp_max(float v) {
 
 constexpr int kTableStages = 256;  // stage-window ring in shared memory
 constexpr int kTableBatch = 128;   // windows computed per refill (one per thread)
-constexpr int kMaxRing = 3;        // TMA raw-sample ring depth
+constexpr int kMaxRing = 4;        // deepest TMA raw-sample ring
 
 // Shared-memory layout of the tiled kernel (byte offsets, all 16-byte aligned).
 struct SmemLayout {
