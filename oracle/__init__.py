@@ -102,6 +102,11 @@ def _load():
             lib.or_logclip_backward.argtypes = [dp, C.c_int64, C.c_double, C.c_int32, C.c_double,
                                                 C.c_double, dp, dp]
             lib.or_logclip_backward.restype = None
+            lib.or_fir.argtypes = [dp, C.c_int32, dp, C.c_int32, dp]
+            lib.or_fir.restype = None
+            lib.or_iq_demod.argtypes = [dp, C.c_int32, C.c_double, C.c_double, dp, C.c_int32,
+                                        C.c_int32, dp]
+            lib.or_iq_demod.restype = None
             _lib = lib
     return _lib
 
@@ -405,6 +410,38 @@ def logclip_backward(env, g_db, ref=None, lo=-60.0, hi=0.0) -> np.ndarray:
     out = np.zeros_like(e)
     _load().or_logclip_backward(_dp(e), e.size, r, int(ref is None), lo, hi, _dp(g), _dp(out))
     return out
+
+
+def fir(x, taps) -> np.ndarray:
+    """FIR of every trace along the last axis (centre tap at lag 0); x [..., ns]."""
+    xx = _f64(x)
+    h = _f64(taps)
+    flat = xx.reshape(-1, xx.shape[-1])
+    out = np.zeros_like(flat)
+    lib = _load()
+    for i in range(flat.shape[0]):
+        row = np.ascontiguousarray(flat[i])
+        o = np.zeros(flat.shape[1])
+        lib.or_fir(_dp(row), flat.shape[1], _dp(h), len(h), _dp(o))
+        out[i] = o
+    return out.reshape(xx.shape)
+
+
+def iq_demod(x, f0, fs, taps, decim: int = 1) -> np.ndarray:
+    """Complex baseband of every trace (mix by f0, FIR low-pass, keep every decim-th sample)."""
+    xx = _f64(x)
+    h = _f64(taps)
+    flat = xx.reshape(-1, xx.shape[-1])
+    ns = flat.shape[1]
+    n_out = -(-ns // decim)
+    out = np.zeros((flat.shape[0], n_out), dtype=np.complex128)
+    lib = _load()
+    for i in range(flat.shape[0]):
+        row = np.ascontiguousarray(flat[i])
+        o = np.zeros(2 * n_out)
+        lib.or_iq_demod(_dp(row), ns, float(f0), float(fs), _dp(h), len(h), int(decim), _dp(o))
+        out[i] = o[0::2] + 1j * o[1::2]
+    return out.reshape(xx.shape[:-1] + (n_out,))
 
 
 def das(case, frame: int = 0, threads: int = 1, rows=None) -> np.ndarray:

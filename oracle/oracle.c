@@ -459,3 +459,49 @@ void or_logclip_backward(const double* env, int64_t n, double ref, int32_t ref_i
     }
     if (ref_is_max && arg >= 0) g_env[arg] += s_ref;
 }
+
+/*
+ * FIR filtering of one RF trace (pre-processing, Sec. II-B "Signal Processing
+ * Operators": FIR filter).  Reading: a causal filter of odd length L with its
+ * centre tap at lag 0, y[n] = sum_{k=0}^{L-1} h[k] x[n + (L-1)/2 - k], x = 0
+ * outside [0, ns); for symmetric (linear-phase) taps this is zero-phase.
+ */
+void or_fir(const double* x, int32_t ns, const double* h, int32_t n_taps, double* y)
+{
+    int32_t c = (n_taps - 1) / 2;
+    for (int32_t n = 0; n < ns; ++n) {
+        double acc = 0.0;
+        for (int32_t k = 0; k < n_taps; ++k) {
+            int64_t i = (int64_t)n + c - k;
+            if (i >= 0 && i < ns) acc += h[k] * x[i];
+        }
+        y[n] = acc;
+    }
+}
+
+/*
+ * IQ demodulation of one RF trace: mix down by the centre frequency f0,
+ * low-pass with the FIR h (same alignment as or_fir), keep every D-th sample:
+ *   iq[m] = sum_k h[k] x[i] exp(-2 pi i f0 i / fs),  i = m D + (L-1)/2 - k.
+ * The mixing phase uses the absolute sample index, so sample m of the output is
+ * the baseband value at time m D / fs.  Writes n_out = ceil(ns / D) complex
+ * samples as (re, im) pairs.
+ */
+void or_iq_demod(const double* x, int32_t ns, double f0, double fs, const double* h,
+                 int32_t n_taps, int32_t decim, double* iq)
+{
+    int32_t c = (n_taps - 1) / 2;
+    int32_t n_out = (ns + decim - 1) / decim;
+    for (int32_t m = 0; m < n_out; ++m) {
+        double re = 0.0, im = 0.0;
+        for (int32_t k = 0; k < n_taps; ++k) {
+            int64_t i = (int64_t)m * decim + c - k;
+            if (i < 0 || i >= ns) continue;
+            double ph = 2.0 * M_PI * f0 * (double)i / fs;
+            re += h[k] * x[i] * cos(ph);
+            im -= h[k] * x[i] * sin(ph);
+        }
+        iq[2 * m] = re;
+        iq[2 * m + 1] = im;
+    }
+}

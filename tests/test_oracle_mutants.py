@@ -12,6 +12,7 @@ import subprocess
 import pytest
 
 import oracle
+import test_oracle_fir_pins as fir_pins
 import test_oracle_grad_pins as grad_pins
 import test_oracle_pins as pins
 
@@ -66,12 +67,27 @@ MUTANTS = {
                                 ["test_logclip_backward_matches_central_difference_including_the_frame_max"]),
     "logclip_bwd_ref_dropped": ("if (ref_is_max && arg >= 0) g_env[arg] += s_ref;", "",
                                 ["test_logclip_backward_matches_central_difference_including_the_frame_max"]),
+    "fir_correlation_for_convolution": ("int64_t i = (int64_t)n + c - k;", "int64_t i = (int64_t)n - c + k;",
+                                        ["test_fir_impulse_response_is_the_taps",
+                                         "test_fir_equals_same_mode_convolution"]),
+    "iq_mix_sign": ("im -= h[k] * x[i] * sin(ph);", "im += h[k] * x[i] * sin(ph);",
+                    ["test_iq_demod_of_a_tone_at_f0"]),
+    "iq_decimation_offset": ("int64_t i = (int64_t)m * decim + c - k;", "int64_t i = (int64_t)m * decim - k;",
+                             ["test_iq_demod_at_zero_frequency_is_the_fir", "test_iq_demod_of_a_tone_at_f0"]),
     "window_width": ("double half_width = 0.5 * z / p->f_number;", "double half_width = z / p->f_number;",
                      ["test_window_is_apod_without_weight", "test_adjoint_identity"]),
 }
 
 
 def _call(name, golden):
+    if hasattr(fir_pins, name):
+        fn = getattr(fir_pins, name)
+        if "n_taps" in fn.__code__.co_varnames[: fn.__code__.co_argcount]:
+            for n_taps in (1, 7, 31):
+                fn(n_taps=n_taps)
+            return
+        fn()
+        return
     if hasattr(grad_pins, name):
         fn = getattr(grad_pins, name)
         if "k" in fn.__code__.co_varnames[: fn.__code__.co_argcount]:
