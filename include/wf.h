@@ -83,6 +83,7 @@ typedef struct {
 #define WF_MAX_ELEMENTS 1024
 #define WF_MAX_TX 256          /* transmits (STAI) or angles (PWI) per frame */
 #define WF_MAX_SAMPLES (1 << 20)
+#define WF_MAX_TAPS 255        /* FIR taps (odd count) */
 
 /*
  * Bytes of device workspace wf_das_stai / wf_das_pwi need for this probe,
@@ -270,6 +271,41 @@ wf_status wf_logclip_backward(const float* env, int32_t batch, int32_t nz, int32
                               const float* ref, int32_t ref_is_frame_max, float db_min,
                               float db_max, const float* grad_db, float* grad_env,
                               wf_stream stream);
+
+/*
+ * Pre-processing (Sec. II-B "Signal Processing Operators": FIR filter).
+ *
+ * wf_fir: every trace (n_samples contiguous values) is filtered by the
+ * odd-length FIR h (centre tap at lag 0, zero-phase for symmetric taps):
+ *   out[n] = sum_{k<L} h[k] x[n + (L-1)/2 - k],  x = 0 outside [0, n_samples)
+ * in FP32; int16 values are multiplied by rf_scale first.
+ *
+ *  rf           device [n_traces][n_samples] of dtype (4-byte aligned)
+ *  taps         host float [n_taps], n_taps odd, 1..WF_MAX_TAPS
+ *  out          device float [n_traces][n_samples]; may not alias rf
+ */
+wf_status wf_fir(const void* rf, wf_dtype dtype, float rf_scale, int64_t n_traces,
+                 int32_t n_samples, const float* taps, int32_t n_taps, float* out,
+                 wf_stream stream);
+
+/*
+ * wf_iq_demod: complex baseband of every trace: mix down by f0 with the
+ * absolute sample phase, low-pass with the FIR h (alignment as wf_fir) and
+ * keep every decim-th sample:
+ *   iq[m] = sum_{k<L} h[k] x[i] exp(-2 pi i f0 i / fs),  i = m decim + (L-1)/2 - k
+ * n_out = ceil(n_samples / decim) complex values per trace, stored as
+ * (re, im) float pairs.  decim 1..16; f0 finite, fs > 0 (Hz).
+ */
+wf_status wf_iq_demod(const void* rf, wf_dtype dtype, float rf_scale, int64_t n_traces,
+                      int32_t n_samples, double f0, double fs, const float* taps,
+                      int32_t n_taps, int32_t decim, float* out_iq, wf_stream stream);
+
+/*
+ * Host utility: windowed-sinc band-pass taps (Hamming window) for wf_fir,
+ * pass band [f_lo, f_hi] Hz at sampling rate fs (f_lo = 0: low-pass).
+ * taps_out: host float [n_taps], n_taps odd, 1..WF_MAX_TAPS.
+ */
+wf_status wf_fir_bandpass(double f_lo, double f_hi, double fs, int32_t n_taps, float* taps_out);
 
 /*
  * STAI delay-and-sum exactly as wf_das_stai, without a caller workspace.

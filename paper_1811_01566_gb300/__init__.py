@@ -23,8 +23,8 @@ from . import _build
 
 __all__ = ["Probe", "Grid", "WfError", "HANN", "RECT", "NONE", "das_stai", "das_pwi",
            "das_workspace_bytes", "das_delays", "das_backward", "das", "envelope", "logclip",
-           "envelope_backward", "logclip_backward", "bmode", "bmode_diff", "workspace_check",
-           "library_path", "version"]
+           "envelope_backward", "logclip_backward", "bmode", "bmode_diff", "fir", "iq_demod",
+           "fir_bandpass", "workspace_check", "library_path", "version"]
 
 HANN, RECT, NONE = 0, 1, 2
 _DTYPES = {torch.float32: 0, torch.float16: 1, torch.int16: 2}
@@ -90,6 +90,14 @@ def _load():
             lib.wf_envelope_backward.restype = C.c_int
             lib.wf_logclip_backward.argtypes = [vp, i32, i32, i32, vp, i32, f32, f32, vp, vp, vp]
             lib.wf_logclip_backward.restype = C.c_int
+            i64 = C.c_int64
+            lib.wf_fir.argtypes = [vp, i32, f32, i64, i32, C.POINTER(C.c_float), i32, vp, vp]
+            lib.wf_fir.restype = C.c_int
+            lib.wf_iq_demod.argtypes = [vp, i32, f32, i64, i32, f64, f64, C.POINTER(C.c_float), i32,
+                                        i32, vp, vp]
+            lib.wf_iq_demod.restype = C.c_int
+            lib.wf_fir_bandpass.argtypes = [f64, f64, f64, i32, C.POINTER(C.c_float)]
+            lib.wf_fir_bandpass.restype = C.c_int
             lib.wf_workspace_check.argtypes = [vp, sz, vp]
             lib.wf_workspace_check.restype = C.c_int
             lib.wf_status_string.argtypes = [C.c_int]
@@ -429,6 +437,50 @@ def bmode_diff(rf: torch.Tensor, probe: Probe, grid: Grid, mode: str, *, elem_we
     reverse-mode kernels."""
     bf = das(rf, probe, grid, mode, elem_weight=elem_weight, c=c, **scan)
     return _LogClip.apply(_Envelope.apply(bf), float(db_min), float(db_max))
+
+
+def _traces(rf: torch.Tensor):
+    if not (rf.is_cuda and rf.dtype in _DTYPES and rf.is_contiguous() and rf.dim() >= 1):
+        raise ValueError("rf must be a contiguous CUDA float32/float16/int16 tensor [..., n_samples]")
+    ns = rf.shape[-1]
+    return rf, ns, rf.numel() // max(ns, 1)
+
+
+def _taps(taps):
+    t = [float(v) for v in taps]
+    return (C.c_float * len(t))(*t), len(t)
+
+
+def fir_bandpass(f_lo: float, f_hi: float, fs: float, n_taps: int) -> list[float]:
+    """Windowed-sinc band-pass taps [f_lo, f_hi] Hz (wf_fir_bandpass)."""
+    buf = (C.c_float * int(n_taps))()
+    _check(_load().wf_fir_bandpass(float(f_lo), float(f_hi), float(fs), int(n_taps), buf),
+           "wf_fir_bandpass")
+    return list(buf)
+
+
+def fir(rf: torch.Tensor, taps, *, rf_scale: float = 1.0, out: torch.Tensor | None = None,
+        stream=None) -> torch.Tensor:
+    """FIR of every trace along the last axis -> float32, same shape (wf_fir)."""
+    rf, ns, n = _traces(rf)
+    out = torch.empty(rf.shape, device=rf.device, dtype=torch.float32) if out is None else out
+    h, nt = _taps(taps)
+    _check(_load().wf_fir(rf.data_ptr(), _DTYPES[rf.dtype], float(rf_scale), n, ns, h, nt,
+                          out.data_ptr(), _stream(stream)), "wf_fir")
+    return out
+
+
+def iq_demod(rf: torch.Tensor, f0: float, fs: float, taps, *, decim: int = 1,
+             rf_scale: float = 1.0, stream=None) -> torch.Tensor:
+    """Complex baseband of every trace -> complex64 [..., ceil(ns / decim)] (wf_iq_demod)."""
+    rf, ns, n = _traces(rf)
+    n_out = -(-ns // int(decim))
+    out = torch.empty(rf.shape[:-1] + (n_out, 2), device=rf.device, dtype=torch.float32)
+    h, nt = _taps(taps)
+    _check(_load().wf_iq_demod(rf.data_ptr(), _DTYPES[rf.dtype], float(rf_scale), n, ns, float(f0),
+                               float(fs), h, nt, int(decim), out.data_ptr(), _stream(stream)),
+           "wf_iq_demod")
+    return torch.view_as_complex(out)
 
 
 def bmode(rf: torch.Tensor, probe: Probe, grid: Grid, *, mode: str, db_min: float = -60.0,

@@ -84,3 +84,14 @@ def test_logclip_edge_values():
     inplace = env.clone()
     wf.logclip(inplace, out=inplace)
     assert inplace[0, 0, 0].item() == pytest.approx(-20 * math.log10(2.0), abs=1e-4)  # max is 2
+
+
+def test_paper_display_range_is_a_shifted_window():
+    """The paper clips to [0, 30] dB (Sec. III): with ref = max * 10^(-30/20) that is the
+    [-30, 0] dB window of the frame maximum shifted by +30 dB."""
+    rng = np.random.default_rng(12)
+    env = torch.from_numpy(rng.uniform(0.0, 2.0, size=(2, 64, 40)).astype(np.float32)).cuda()
+    fmax = env.amax(dim=(1, 2)).contiguous()
+    a = wf.logclip(env, ref=(fmax * 10 ** (-30 / 20)).contiguous(), db_min=0.0, db_max=30.0)
+    b = wf.logclip(env, ref=fmax, db_min=-30.0, db_max=0.0)
+    assert torch.allclose(a, b + 30.0, atol=1e-4)
