@@ -154,7 +154,7 @@ double max_delay(const wf_probe* p, const wf_grid* g) {
 constexpr Cfg kStaiCfgs[] = {{4, 4}, {4, 2}};
 constexpr Cfg kPwiCfgs[] = {{4, 4}, {4, 2}};
 constexpr size_t kSmemBudget = 113 * 1024;   // two CTAs per SM
-constexpr int kTargetItems = 8 * 152;        // CTAs per launch the groups aim for
+constexpr int kTargetItems = 1536;            // CTAs per launch the groups aim for (~10 waves)
 
 // Reciprocal STAI pairing applies when every element fires once, in element
 // order (transmit t fires element t), so rf[t][r] and rf[r][t] share delay and
@@ -207,6 +207,8 @@ Plan plan_for(int mode, const Cfg& cfg, const GeomD& D, const wf_probe* p, const
     P.tiles_z = (g->nz + P.rows - 1) / P.rows;
     const long long tiles = (long long)P.tiles_x * P.tiles_z * batch;
     P.n_groups = (int)std::min<long long>(kMaxGroups, std::max<long long>(1, (kTargetItems + tiles - 1) / tiles));
+    if (const char* v = std::getenv("WF_DAS_GROUPS"))   // tuning override
+        P.n_groups = std::max(1, std::min(kMaxGroups, std::atoi(v)));
     P.n_items = P.tiles_x * P.tiles_z * P.n_groups;
     P.sym = sym && mode == 0;
     // TMA bulk copies need 16-byte aligned trace windows: samples per trace a multiple of 8.

@@ -47,7 +47,7 @@ namespace wf {
 constexpr int kThreads = 256;              // 8 warps
 constexpr int kC = 8;                      // receive elements per chunk
 constexpr int kMaxWindow = 512;            // staged positions per trace: 64 segments of 8
-constexpr int kMaxGroups = 8;              // receive-chunk groups per tile
+constexpr int kMaxGroups = 32;             // receive-chunk groups per tile
 constexpr float kMagic = 12582912.0f;      // 1.5 * 2^23
 constexpr int kMagicBits = 0x4B400000;
 
@@ -482,6 +482,39 @@ __device__ __forceinline__ float warp_max(float v) {
     return v;
 }
 
+// Packed pairs of FP32 values for Blackwell's f32x2 arithmetic: two of a
+// thread's pixels go through one instruction, each lane rounded exactly as the
+// scalar operation would be.
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 x2_pack(float lo, float hi) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void x2_unpack(f32x2 v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f32x2 x2_add(f32x2 a, f32x2 b) {
+    f32x2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 x2_add_rm(f32x2 a, f32x2 b) {
+    f32x2 r;
+    asm("add.rm.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 x2_sub(f32x2 a, f32x2 b) {
+    f32x2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 x2_fma(f32x2 a, f32x2 b, f32x2 c) {
+    f32x2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
 constexpr int kTableStages = 256;  // stage-window ring in shared memory
 constexpr int kTableBatch = 128;   // windows computed per refill (one per thread)
 constexpr int kMaxRing = 4;        // deepest TMA raw-sample ring
@@ -744,13 +777,16 @@ __global__ void __launch_bounds__(kThreads, 2) das_tiled_kernel(const __grid_con
     const float wux0 = (float)(WCOL * warp) * g.gdx, wux1 = (float)(WCOL * warp + WCOL - 1) * g.gdx;
     const float wuz1 = (float)(S::kRows - 1) * g.gdz;
 
+    static_assert(P % 2 == 0, "pixels per lane are processed in packed pairs");
+    constexpr int H = P / 2;
     float acc[P];
 #pragma unroll
     for (int p = 0; p < P; ++p) acc[p] = 0.0f;
-    float Dr[kC][P], Wr[kC][P];
+    f32x2 Dr2[kC][H], Wr2[kC][H];   // receive distances / weights of pixel pairs (2h, 2h + 1)
     float dr_min = 0.0f, dr_max = 0.0f;
     unsigned cmask = 0u;
     RegStage<T, SYM> rs;
+    const f32x2 kMagic2 = x2_pack(kMagic, kMagic);
 
     if (TMA) {
         if (warp == 0)
@@ -838,14 +874,20 @@ __global__ void __launch_bounds__(kThreads, 2) das_tiled_kernel(const __grid_con
                     const bool on = (cmask >> c) & 1u;
                     const Elem ee = el[(on ? r0 + c : r0) - er.x];
                     const float cc = elem_rel(ee, e0);
+                    float d[P], w[P];
 #pragma unroll
                     for (int p = 0; p < P; ++p) {
-                        Dr[c][p] = on ? cc + dist_delta(ee, ux, kz[p]) : 0.0f;
-                        Wr[c][p] = on ? apod_w(g.apod, -(ee.ax + ux), kap[p]) * (ee.g * a.rf_scale) : 0.0f;
+                        d[p] = on ? cc + dist_delta(ee, ux, kz[p]) : 0.0f;
+                        w[p] = on ? apod_w(g.apod, -(ee.ax + ux), kap[p]) * (ee.g * a.rf_scale) : 0.0f;
                         if (on) {
-                            mn = fminf(mn, Dr[c][p]);
-                            mx = fmaxf(mx, Dr[c][p]);
+                            mn = fminf(mn, d[p]);
+                            mx = fmaxf(mx, d[p]);
                         }
+                    }
+#pragma unroll
+                    for (int h = 0; h < H; ++h) {
+                        Dr2[c][h] = x2_pack(d[2 * h], d[2 * h + 1]);
+                        Wr2[c][h] = x2_pack(w[2 * h], w[2 * h + 1]);
                     }
                 }
                 dr_min = warp_min(mn);
@@ -893,29 +935,44 @@ __global__ void __launch_bounds__(kThreads, 2) das_tiled_kernel(const __grid_con
             }
         }
         if (live) {
-            float acct[P];
+            // Per pixel: s = tw + Dr, i = floor(s) by the round-down add of 1.5 * 2^23,
+            // f = s - i, v = x[i] + f (x[i+1] - x[i]), acc += Wr v -- two pixels per
+            // packed instruction.
+            f32x2 tw2[H], acct2[H];
 #pragma unroll
-            for (int p = 0; p < P; ++p) acct[p] = 0.0f;
+            for (int h = 0; h < H; ++h) {
+                tw2[h] = x2_pack(tw[2 * h], tw[2 * h + 1]);
+                acct2[h] = 0ull;
+            }
 #pragma unroll
             for (int c = 0; c < kC; ++c) {
                 if (!((cm >> c) & 1u)) continue;
                 const float2* bc = buf + c * a.W;
 #pragma unroll
-                for (int p = 0; p < P; ++p) {
-                    const float s = tw[p] + Dr[c][p];
-                    const float m = __fadd_rd(s, kMagic);
-                    const float f = s - (m - kMagic);
-                    int idx = __float_as_int(m) - kMagicBits;
-                    if (CHECK && (idx < 0 || idx >= si.len)) {
-                        flag(a.hdr, 2u, (unsigned)blockIdx.x, (unsigned)idx, (unsigned)si.len);
-                        idx = 0;
+                for (int h = 0; h < H; ++h) {
+                    const f32x2 s2 = x2_add(tw2[h], Dr2[c][h]);
+                    const f32x2 m2 = x2_add_rm(s2, kMagic2);
+                    const f32x2 f2 = x2_sub(s2, x2_sub(m2, kMagic2));
+                    float m0, m1;
+                    x2_unpack(m2, m0, m1);
+                    int i0 = __float_as_int(m0) - kMagicBits, i1 = __float_as_int(m1) - kMagicBits;
+                    if (CHECK && (i0 < 0 || i0 >= si.len || i1 < 0 || i1 >= si.len)) {
+                        flag(a.hdr, 2u, (unsigned)blockIdx.x, (unsigned)min(i0, i1), (unsigned)si.len);
+                        i0 = 0;
+                        i1 = 0;
                     }
-                    const float2 ab = bc[idx];
-                    acct[p] = fmaf(Wr[c][p], fmaf(f, ab.y, ab.x), acct[p]);
+                    const float2 a0 = bc[i0], a1 = bc[i1];
+                    const f32x2 v2 = x2_fma(f2, x2_pack(a0.y, a1.y), x2_pack(a0.x, a1.x));
+                    acct2[h] = x2_fma(Wr2[c][h], v2, acct2[h]);
                 }
             }
 #pragma unroll
-            for (int p = 0; p < P; ++p) acc[p] = MODE == 0 ? fmaf(wt[p], acct[p], acc[p]) : acc[p] + acct[p];
+            for (int h = 0; h < H; ++h) {
+                float t0, t1;
+                x2_unpack(acct2[h], t0, t1);
+                acc[2 * h] = MODE == 0 ? fmaf(wt[2 * h], t0, acc[2 * h]) : acc[2 * h] + t0;
+                acc[2 * h + 1] = MODE == 0 ? fmaf(wt[2 * h + 1], t1, acc[2 * h + 1]) : acc[2 * h + 1] + t1;
+            }
         }
         if (!DB) __syncthreads();   // single buffer: compute of stage q done before stage q + 1 lands
     }

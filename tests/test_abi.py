@@ -67,7 +67,9 @@ def test_workspace_query_is_host_only_and_scales_with_batch():
     a = wf.das_workspace_bytes(pr, gr, 1, 32)
     b = wf.das_workspace_bytes(pr, gr, 4, 32)
     assert a > 256 and b > a
-    assert (b - 256) == 4 * (a - 256)
+    # partial tiles grow with the batch; fewer receive-chunk groups per tile are
+    # needed to fill the GPU when there are more frames, so the growth is sublinear
+    assert (b - 256) <= 4 * (a - 256)
 
 
 @pytest.mark.parametrize("bad", [
