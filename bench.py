@@ -86,7 +86,7 @@ def make_case(name, device):
 # ----------------------------------------------------------------------------- geometry counts
 
 def delay_sum_counts(case, device):
-    """Exact (dense, aperture-active, contributing, contributing per row) delay-sum counts, FP64.
+    """Exact (dense, aperture-active, contributing, contributing per pixel [nz][nx]) delay-sum counts.
 
     active: both weights non-zero; contributing: active and the interpolated
     sample lies inside the record (0 <= floor(s) <= ns - 2).  Bookkeeping for
@@ -103,7 +103,7 @@ def delay_sum_counts(case, device):
     n_tx = case.n_tx
     dense = case.nz * case.nx * n_tx * e
     active = contributing = 0
-    per_row = []
+    per_px = []
     rows = max(1, int(2 ** 25 // (case.nx * n_tx * e)))
     for r0 in range(0, case.nz, rows):
         z = zs[r0:r0 + rows][:, None].expand(-1, case.nx).reshape(-1)
@@ -126,10 +126,10 @@ def delay_sum_counts(case, device):
         fl = torch.floor(s)
         ok = act & (fl >= 0) & (fl <= case.n_samples - 2)
         active += int(act.sum())
-        row_ok = ok.reshape(-1, case.nx * n_tx * e).sum(1)
-        per_row += [int(v) for v in row_ok.cpu()]
-        contributing += int(row_ok.sum())
-    return dense, active, contributing, per_row
+        px_ok = ok.reshape(-1, n_tx * e).sum(1)
+        per_px.append(px_ok.cpu().numpy())
+        contributing += int(px_ok.sum())
+    return dense, active, contributing, np.concatenate(per_px).reshape(case.nz, case.nx)
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -194,40 +194,54 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- CPU oracle sample
 
-def oracle_sample(case, seconds, counts_rows, start=0):
-    """Time the FP64 oracle on a strided subset of image rows (single thread) and scale.
+def oracle_sample(case, seconds, counts_px, start=0):
+    """Time the FP64 oracle (single thread) on a bounded sample of the frame and scale.
 
-    Returns (frames_per_s, sample_description, seconds spent).  Rows are taken
-    every 7th from ``start`` (then the rest), until the time budget is used; DAS
-    time is scaled by the contributing-delay-sum fraction of the sampled rows;
-    envelope and log-clip are timed on a few columns and scaled by column count.
+    DAS runs on runs of 16 pixels of one image row (a 1 x 16 sub-grid with exactly
+    those pixels' positions), visited in a fixed pseudo-random order from ``start``
+    until ``seconds`` is used (at least one run); its time is scaled by the
+    contributing-delay-sum fraction of the sampled pixels.  Envelope and log-clip run
+    on one image column and are scaled by the column count.
+    Returns (frames_per_s, sample description, seconds spent, (DAS seconds, work
+    fraction, post-processing seconds per frame)) -- the last for pooling samples.
     """
     import oracle
-    order = [(start + 7 * i) % case.nz for i in range(-(-case.nz // 7))]
-    order = list(dict.fromkeys(order)) + [r for r in range(case.nz) if r not in set(order)]
-    done, t_das, work = [], 0.0, 0
-    total_work = float(sum(counts_rows))
-    for r in order:
+    pr, gr = oracle.probe_grid(case)
+    rf = case.rf64[0]
+    runs = [(r, c) for r in range(case.nz) for c in range(0, case.nx, 16)]
+    order = np.random.default_rng(12345).permutation(len(runs))
+    total_work = float(counts_px.sum())
+
+    def pos(axis_min, axis_max, n, i):
+        return axis_min + i * (axis_max - axis_min) / (n - 1) if n > 1 else axis_min
+
+    t_das, work, n_px, k = 0.0, 0, 0, 0
+    while True:
+        r, c0 = runs[order[(start + k) % len(runs)]]
+        k += 1
+        c1 = min(case.nx, c0 + 16)
+        z = pos(case.z_min, case.z_max, case.nz, r)
+        sub = oracle.Grid(1, c1 - c0, pos(case.x_min, case.x_max, case.nx, c0),
+                          pos(case.x_min, case.x_max, case.nx, c1 - 1), z, z)
         t0 = time.perf_counter()
-        oracle.das(case, 0, threads=1, rows=(r, r + 1))
+        if case.mode == "stai":
+            oracle.das_stai(rf, pr, sub, tx_elem=case.tx_elem, t_start=case.t_start)
+        else:
+            oracle.das_pwi(rf, pr, sub, angles=case.angles, t_starts=case.t_starts)
         t_das += time.perf_counter() - t0
-        done.append(r)
-        work += counts_rows[r]
-        if t_das > 0.85 * seconds and work > 0:
+        work += int(counts_px[r, c0:c1].sum())
+        n_px += c1 - c0
+        if (t_das > 0.8 * seconds and work > 0) or k >= len(runs):
             break
-    frac = work / total_work if total_work > 0 else len(done) / case.nz
+    frac = work / total_work if total_work > 0 else n_px / (case.nz * case.nx)
     das_frame = t_das / max(frac, 1e-12)
-    cols = min(case.nx, 4)
-    bf = np.random.default_rng(0).normal(size=(case.nz, cols))
+    col = np.random.default_rng(0).normal(size=(case.nz, 1))
     t0 = time.perf_counter()
-    env = oracle.envelope(bf)
-    oracle.logclip(env)
-    t_post = (time.perf_counter() - t0) * case.nx / cols
-    frame = das_frame + t_post
-    desc = (f"{len(done)} of {case.nz} image rows (every 7th from row {start} first; {work} of {int(total_work)} "
-            f"contributing delay-sums) + {cols} envelope/log-clip columns, single thread, "
-            f"scaled to one frame")
-    return 1.0 / frame, desc, t_das + t_post
+    oracle.logclip(oracle.envelope(col))
+    t_post = (time.perf_counter() - t0) * case.nx
+    desc = (f"{n_px} of {case.nz * case.nx} pixels in runs of 16 ({work} of {int(total_work)} "
+            f"contributing delay-sums) + 1 envelope/log-clip column, single thread, scaled to one frame")
+    return 1.0 / (das_frame + t_post), desc, t_das + t_post / case.nx, (t_das, frac, t_post)
 
 
 # ----------------------------------------------------------------------------- native arm
@@ -385,7 +399,7 @@ def run_native(args, rank, world, local_rank):
 
     if rank != 0:
         return None
-    dense, active, contributing, per_row = delay_sum_counts(case, dev)
+    dense, active, contributing, per_px = delay_sum_counts(case, dev)
     frames = args.steps * b * world
     fps = frames / (ms / 1e3)
     props = torch.cuda.get_device_properties(dev)
@@ -452,7 +466,7 @@ def run_native(args, rank, world, local_rank):
     if not args.no_cpu_baseline:
         cpu_case = case if case.batch == 1 else None
         if cpu_case is not None:
-            v, desc, spent = oracle_sample(case, args.cpu_seconds, per_row)
+            v, desc, spent, _ = oracle_sample(case, args.cpu_seconds, per_px)
             line["cpu_baseline"] = {"value": round(v, 6), "unit": "frames/s", "cores": 1,
                                     "kind": "oracle", "sample": desc,
                                     "cpu": _cpu_model(), "seconds": round(spent, 2)}
@@ -651,16 +665,18 @@ def run_reference(args):
     case = make_case(args.workload, dev)
     counts = delay_sum_counts(case, dev or "cpu")[3]
     # the whole run stays near two minutes whatever K is: each step is a bounded sample
-    per_step = min(args.cpu_seconds, 120.0 / max(1, args.steps + args.warmup))
-    for i in range(args.warmup):
-        oracle_sample(case, per_step, counts, start=(97 * i) % case.nz)
-    vals, spent = [], 0.0
+    per_step = min(args.cpu_seconds, 100.0 / max(1, args.steps + args.warmup))
+    spent, t_das, frac, t_post = 0.0, 0.0, 0.0, []
     desc = ""
-    for i in range(args.steps):
-        v, desc, s = oracle_sample(case, per_step, counts, start=(97 * (i + args.warmup)) % case.nz)
-        vals.append(v)
-        spent += s
-    fps = statistics.mean(vals)
+    for i in range(args.warmup + args.steps):
+        _, desc, s, parts = oracle_sample(case, per_step, counts, start=7 * i)
+        if i >= args.warmup:
+            spent += s
+            t_das += parts[0]
+            frac += parts[1]
+            t_post.append(parts[2])
+    # pooled over the steps (ratio of sums): DAS seconds per frame + post-processing seconds
+    fps = 1.0 / (t_das / max(frac, 1e-12) + statistics.mean(t_post))
     line = {
         "impl": "reference",
         "metric": "DAS frames/s (B-mode: delay-and-sum + envelope + log-clip per frame)",
@@ -678,7 +694,7 @@ def run_reference(args):
         "config": {"workload": f"{args.workload}: {WORKLOAD_TEXT[args.workload]}",
                    "frames_per_step": 1, "parallelism": "single CPU thread"},
         "cpu_baseline": {"value": round(fps, 6), "unit": "frames/s", "cores": 1, "kind": "oracle",
-                         "sample": f"per step, {desc}; mean over {args.steps} steps",
+                         "sample": f"per step, {desc}; pooled over {args.steps} steps",
                          "cpu": _cpu_model(), "seconds": round(spent, 2)},
         "e2e": {"value": round(fps, 6), "unit": "frames/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
