@@ -5,6 +5,8 @@
 // das_check.cu (bounds-checked variants).
 #include <algorithm>
 #include <cmath>
+#include <numeric>
+#include <vector>
 #include <cstdlib>
 #include <cstdio>
 #include <cstring>
@@ -154,7 +156,8 @@ double max_delay(const wf_probe* p, const wf_grid* g) {
 constexpr Cfg kStaiCfgs[] = {{4, 4}, {4, 2}};
 constexpr Cfg kPwiCfgs[] = {{4, 4}, {4, 2}};
 constexpr size_t kSmemBudget = 113 * 1024;   // two CTAs per SM
-constexpr int kTargetItems = 1536;            // CTAs per launch the groups aim for (~10 waves)
+constexpr int kTargetItems = 1536;            // CTAs per frame the groups aim for (~5 waves)
+constexpr int kTargetItemsStai = 768;
 
 // Reciprocal STAI pairing applies when every element fires once, in element
 // order (transmit t fires element t), so rf[t][r] and rf[r][t] share delay and
@@ -210,6 +213,15 @@ Plan plan_for(int mode, const Cfg& cfg, const GeomD& D, const wf_probe* p, const
     if (const char* v = std::getenv("WF_DAS_GROUPS"))   // tuning override
         P.n_groups = std::max(1, std::min(kMaxGroups, std::atoi(v)));
     P.n_items = P.tiles_x * P.tiles_z * P.n_groups;
+    // Work-proportional schedule (built per call from the scan geometry): budget CTAs per
+    // frame plus at most one extra per tile from rounding.
+    // CTAs per frame: reciprocal STAI tiles carry more start-up per stage (window
+    // bounds of pair sums, two traces per row), so they take fewer, longer CTAs.
+    long long target_items = mode == 0 ? kTargetItemsStai : kTargetItems;
+    if (const char* v = std::getenv("WF_DAS_BUDGET")) target_items = std::max(1, std::atoi(v));   // tuning
+    P.budget = (int)std::max<long long>(1, (target_items + batch - 1) / batch);
+    P.table = (long long)P.budget + P.tiles_x * P.tiles_z <= kMaxItems && !std::getenv("WF_DAS_GROUPS");
+    P.info_bytes = (((size_t)P.tiles_x * P.tiles_z * sizeof(unsigned)) + 255) & ~(size_t)255;
     P.sym = sym && mode == 0;
     // TMA bulk copies need 16-byte aligned trace windows: samples per trace a multiple of 8.
     // WF_DAS_NO_TMA=1 selects the register-staged path instead (tuning and testing).
@@ -246,8 +258,9 @@ Plan plan_for(int mode, const Cfg& cfg, const GeomD& D, const wf_probe* p, const
         P.smem = smem_layout(P.W, p->n_elements, false, P.tma, P.sym, P.ring, rf_bytes).total;
         if (P.smem > kMaxTiledSmem) P.tiled = false;
     }
-    P.ws_bytes = kWsHeaderBytes +
-                 (P.tiled ? (size_t)batch * P.n_items * kThreads * cfg.p * sizeof(float) : 0);
+    const long long item_bound = P.table ? (long long)P.budget + P.tiles_x * P.tiles_z : P.n_items;
+    P.ws_bytes = kWsHeaderBytes + P.info_bytes +
+                 (P.tiled ? (size_t)batch * item_bound * kThreads * cfg.p * sizeof(float) : 0);
     return P;
 }
 
@@ -290,6 +303,82 @@ wf_status dispatch(DasArgs& A, const Plan& P, int batch, wf_dtype dt, cudaStream
                                : launch_das_tiled<MODE, false>(A, P, batch, dt, st);
 }
 
+// Schedule of a frame's CTAs.  For every tile, an upper estimate of the
+// (transmit, receive) pairs whose delay can reach the record (0 only when the
+// smallest possible delay of every pair lies beyond the record: the tile's
+// image is exactly 0 and it gets no CTA).  Every other tile gets the same
+// number of groups (equal ranges of its stage list), budget / live tiles, and
+// tiles are launched heaviest first.  (Groups in proportion to each tile's work
+// were measured slower: they cut the heavy tiles into CTAs too short to amortise
+// a CTA's start-up.)  Returns the number of items.
+int build_schedule(int mode, const wf_probe* p, const wf_grid* g, const Plan& P, DasArgs& A) {
+    Geom G;
+    GeomD D;
+    make_geom(p, g, G, D);
+    const int E = p->n_elements, tiles = P.tiles_x * P.tiles_z;
+    const double L = (double)A.ns + 16.0;                 // beyond this a window misses the record
+    std::vector<double> work(tiles, 0.0), dmin(E), d;
+    for (int tz = 0; tz < P.tiles_z; ++tz)
+        for (int tx = 0; tx < P.tiles_x; ++tx) {
+            const int ix0 = tx * P.cols, iz0 = tz * P.rows;
+            const double xlo = D.gx0 + ix0 * D.gdx, xhi = D.gx0 + (ix0 + P.cols - 1) * D.gdx;
+            const double zlo = D.gz0 + iz0 * D.gdz, zhi = D.gz0 + (iz0 + P.rows - 1) * D.gdz;
+            int lo = 0, hi = E - 1;
+            if (p->apod != WF_APOD_NONE) {
+                if (!(zhi > 0.0)) continue;                    // no aperture anywhere in the tile
+                const double half = zhi / (2.0 * p->f_number);
+                lo = std::max(0, (int)std::floor((xlo - half - D.xe0) / D.pitch) - 2);
+                hi = std::min(E - 1, (int)std::ceil((xhi + half - D.xe0) / D.pitch) + 2);
+                if (lo > hi) continue;
+            }
+            // smallest distance from each element to the tile (its top edge)
+            for (int e = 0; e < E; ++e) {
+                const double xe = D.xe0 + e * D.pitch;
+                const double dx = xe < xlo ? xlo - xe : (xe > xhi ? xe - xhi : 0.0);
+                dmin[e] = std::sqrt(dx * dx + zlo * zlo);
+            }
+            d.assign(dmin.begin() + lo, dmin.begin() + hi + 1);
+            std::sort(d.begin(), d.end());
+            double cnt = 0.0;
+            auto upto = [&](double v) { return (double)(std::upper_bound(d.begin(), d.end(), v) - d.begin()); };
+            if (mode == 0) {
+                if (P.sym) {   // pairs t <= r of the element range
+                    const double lim = L + A.tx[0].t0.hi;
+                    for (size_t i = 0; i < d.size(); ++i) cnt += std::max(0.0, upto(lim - d[i]) - (double)i);
+                } else {
+                    for (int t = 0; t < A.n_tx; ++t) {
+                        const int e = A.tx[t].e;
+                        if (e < lo || e > hi) continue;
+                        cnt += upto(L + A.tx[t].t0.hi - dmin[e]);
+                    }
+                }
+            } else {
+                for (int t = 0; t < A.n_tx; ++t) {
+                    const double sn = (double)A.tx[t].sin.hi + A.tx[t].sin.lo;
+                    const double cs = (double)A.tx[t].cos.hi + A.tx[t].cos.lo;
+                    const double c0 = std::min(xlo * sn, xhi * sn) + zlo * cs - A.tx[t].t0.hi;
+                    cnt += upto(L - c0);
+                }
+            }
+            work[tz * P.tiles_x + tx] = cnt;
+        }
+    const double total = std::accumulate(work.begin(), work.end(), 0.0);
+    if (!(total > 0.0)) return 0;
+    std::vector<int> order(tiles);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work[x] > work[y]; });
+    int live_tiles = 0;
+    for (int t = 0; t < tiles; ++t) live_tiles += work[t] > 0.0;
+    const int grp = std::max(1, std::min(kMaxGroups, (P.budget + live_tiles / 2) / live_tiles));
+    int n = 0;
+    for (int tile : order) {
+        if (!(work[tile] > 0.0)) break;
+        for (int k = 0; k < grp && n < kMaxItems; ++k)
+            A.items[n++] = (unsigned)tile | ((unsigned)k << 16) | ((unsigned)grp << 24);
+    }
+    return n;
+}
+
 wf_status das_common(int mode, const wf_probe* probe, const wf_grid* grid, int32_t batch,
                      int32_t n_tx, int32_t n_rx, int32_t n_samples, wf_dtype dtype,
                      const void* rf, float rf_scale, float* out, void* ws, size_t ws_bytes,
@@ -322,10 +411,16 @@ wf_status das_common(int mode, const wf_probe* probe, const wf_grid* grid, int32
     A.rf_scale = dtype == WF_I16 ? rf_scale : 1.0f;
     A.frame_elems = (long long)n_tx * probe->n_elements * n_samples;
     A.hdr = static_cast<WsHeader*>(ws);
-    A.part = reinterpret_cast<float*>(static_cast<char*>(ws) + kWsHeaderBytes);
+    A.tile_info = reinterpret_cast<unsigned*>(static_cast<char*>(ws) + kWsHeaderBytes);
+    A.part = reinterpret_cast<float*>(static_cast<char*>(ws) + kWsHeaderBytes + P.info_bytes);
     A.out = out;
+    A.use_table = 0;
+    if (P.tiled && P.table) {
+        A.use_table = 1;
+        A.n_items = build_schedule(mode, probe, grid, P, A);
+    }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    if ((s = cuda_status(cudaMemsetAsync(ws, 0, kWsHeaderBytes, st))) != WF_OK) return s;
+    if ((s = cuda_status(cudaMemsetAsync(ws, 0, kWsHeaderBytes + P.info_bytes, st))) != WF_OK) return s;
     return mode == 0 ? dispatch<0>(A, P, batch, dtype, st) : dispatch<1>(A, P, batch, dtype, st);
 }
 
@@ -483,6 +578,8 @@ extern "C" wf_status wf_das_backward(const wf_probe* probe, const wf_grid* grid,
     a.part = nullptr;
     a.out = nullptr;
     a.hdr = nullptr;
+    a.use_table = 0;
+    a.tile_info = nullptr;
     a.grad_out = grad_out;
     a.grad_rf = grad_rf;
     a.grad_w = grad_weight;

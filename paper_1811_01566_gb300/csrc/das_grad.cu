@@ -148,29 +148,19 @@ __global__ void __launch_bounds__(kThreads, 2) das_backward_kernel(const __grid_
                 if (MODE == 0 && (a.tx[t].e < er.x || a.tx[t].e > er.y)) continue;
                 s_tlist[n++] = t;
             }
-        const int G = a.n_groups;
-        int ka, kb, q0 = 0;
-        if (SYM) {
-            const long long total = sym_prefix(nc, nc, n_e);
-            ka = 0;
-            while (ka < nc && (long long)sym_prefix(ka, nc, n_e) * G < (long long)group * total) ++ka;
-            kb = ka;
-            while (kb < nc && (long long)sym_prefix(kb, nc, n_e) * G < (long long)(group + 1) * total) ++kb;
-            q0 = sym_prefix(ka, nc, n_e);
-        } else {
-            ka = (group * nc) / G;
-            kb = ((group + 1) * nc) / G;
-        }
+        // This group's share of the tile's raw stage list (chunk-major, every transmit
+        // per chunk): equal raw-stage ranges, so a heavy chunk can span several groups.
+        const long long G = a.n_groups;
+        const long long n_raw = n_e == 0 ? 0 : SYM ? sym_prefix(nc, nc, n_e) : (long long)nc * n;
+        const int qa = (int)((long long)group * n_raw / G), qb = (int)((long long)(group + 1) * n_raw / G);
         s_info[0] = n;
-        s_info[1] = ka;
-        s_info[2] = kb;
-        s_info[3] = q0;
+        s_info[1] = qa;
+        s_info[2] = qb;
     }
     __syncthreads();
-    const int n_act = s_info[0], k_a = s_info[1], k_b = s_info[2], q0 = s_info[3];
-    const int n_stages = n_e == 0 ? 0 : SYM ? sym_prefix(k_b, nc, n_e) - q0 : (k_b - k_a) * n_act;
+    const int n_act = s_info[0], q0 = s_info[1], n_stages = s_info[2] - s_info[1];
 
-    const StageSpace sp{er, n_e, nc, n_act, k_a, q0, n_stages, s_tlist};
+    const StageSpace sp{er, n_e, nc, n_act, q0, n_stages, s_tlist};
     auto tx_of = [&](int j) { return stage_tx<SYM>(sp, j); };
     int n_live = 0, raw_next = 0;
     auto need = [&](int upto) {   // make entry `upto` exist while raw stages are left

@@ -47,7 +47,8 @@ namespace wf {
 constexpr int kThreads = 256;              // 8 warps
 constexpr int kC = 8;                      // receive elements per chunk
 constexpr int kMaxWindow = 512;            // staged positions per trace: 64 segments of 8
-constexpr int kMaxGroups = 32;             // receive-chunk groups per tile
+constexpr int kMaxGroups = 64;             // stage-range groups per tile
+constexpr int kMaxItems = 2048;            // CTAs per frame of a work-proportional schedule
 constexpr float kMagic = 12582912.0f;      // 1.5 * 2^23
 constexpr int kMagicBits = 0x4B400000;
 
@@ -78,6 +79,12 @@ struct DasArgs {
     float* part;                     // [batch][n_items][256 * P] group partials
     float* out;
     WsHeader* hdr;
+    // work-proportional schedule: item i is tile items[i] & 0xffff, group (items[i] >> 16) & 0xff
+    // of items[i] >> 24; each tile's first CTA records (first item + 1) | groups << 24 in
+    // tile_info for the reduction (0: the tile has no CTA and its pixels are 0)
+    int use_table;
+    unsigned* tile_info;
+    unsigned items[kMaxItems];
     // reverse mode (wf_das_backward) only
     const float* grad_out;           // [batch][nz][nx] cotangent of the image
     float* grad_rf;                  // [batch][n_tx][E][ns] or null
@@ -582,13 +589,14 @@ __device__ __forceinline__ void stage_store(const RegStage<T, SYM>& rs, float2* 
     }
 }
 
-// A CTA's stage space: receive chunks [k_a, k_b) of the tile's element range
-// er, chunk-outer, with every active transmit per chunk (reciprocal STAI:
-// transmits up to the chunk's last element).  Raw stage q maps to (chunk k,
-// transmit slot j); slot j is transmit tlist[j], or er.x + j when reciprocal.
+// A CTA's stage space: raw stages [q0, q0 + n_stages) of its tile's list,
+// which runs over the receive chunks of the element range er, chunk-outer, with
+// every active transmit per chunk (reciprocal STAI: transmits up to the
+// chunk's last element).  Raw stage q maps to (chunk k, transmit slot j); slot
+// j is transmit tlist[j], or er.x + j when reciprocal.
 struct StageSpace {
     int2 er;
-    int n_e, nc, n_act, k_a, q0, n_stages;
+    int n_e, nc, n_act, q0, n_stages;
     const int* tlist;
 };
 
@@ -599,8 +607,9 @@ __device__ __forceinline__ void locate_stage(const StageSpace& sp, int q, int& k
         k = sym_chunk(qg, sp.nc);
         j = qg - 4 * k * (k + 1);
     } else {
-        k = sp.k_a + q / sp.n_act;
-        j = q - (q / sp.n_act) * sp.n_act;
+        const int qg = sp.q0 + q;
+        k = qg / sp.n_act;
+        j = qg - k * sp.n_act;
     }
 }
 
@@ -673,8 +682,22 @@ __global__ void __launch_bounds__(kThreads, 2) das_tiled_kernel(const __grid_con
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int lx = lane % WCOL, lz = lane / WCOL;
     const int item = blockIdx.x, b = blockIdx.y;
-    const int group = item % a.n_groups, rank = item / a.n_groups;
-    const int tzi = a.tiles_z - 1 - rank / a.tiles_x, txi = rank % a.tiles_x;
+    int group, n_grp, tzi, txi;
+    if (a.use_table) {
+        const unsigned code = a.items[item];
+        const int tile = (int)(code & 0xffffu);
+        group = (int)((code >> 16) & 0xffu);
+        n_grp = (int)(code >> 24);
+        tzi = tile / a.tiles_x;
+        txi = tile - tzi * a.tiles_x;
+        if (b == 0 && tid == 0 && group == 0) a.tile_info[tile] = (unsigned)(item + 1) | ((unsigned)n_grp << 24);
+    } else {
+        group = item % a.n_groups;
+        n_grp = a.n_groups;
+        const int rank = item / a.n_groups;
+        tzi = a.tiles_z - 1 - rank / a.tiles_x;
+        txi = rank % a.tiles_x;
+    }
     const TileGeo tg = tile_geo<S::kCols, S::kRows>(a, txi * S::kCols, tzi * S::kRows);
     const T* rf = reinterpret_cast<const T*>(a.rf) + (long long)b * a.frame_elems;
     const bool vec_ok = (a.ns & 7) == 0;
@@ -706,34 +729,23 @@ __global__ void __launch_bounds__(kThreads, 2) das_tiled_kernel(const __grid_con
                 if (MODE == 0 && (a.tx[t].e < er.x || a.tx[t].e > er.y)) continue;
                 s_tlist[n++] = t;
             }
-        // This group's receive chunks [ka, kb): equal stage counts per group.
-        const int G = a.n_groups;
-        int ka, kb, q0 = 0;
-        if (SYM) {
-            const long long total = sym_prefix(nc, nc, n_e);
-            ka = 0;
-            while (ka < nc && (long long)sym_prefix(ka, nc, n_e) * G < (long long)group * total) ++ka;
-            kb = ka;
-            while (kb < nc && (long long)sym_prefix(kb, nc, n_e) * G < (long long)(group + 1) * total) ++kb;
-            q0 = sym_prefix(ka, nc, n_e);
-        } else {
-            ka = (group * nc) / G;
-            kb = ((group + 1) * nc) / G;
-        }
+        // This group's share of the tile's raw stage list (chunk-major, every transmit
+        // per chunk): equal raw-stage ranges, so a heavy chunk can span several groups.
+        const long long G = n_grp;
+        const long long n_raw = n_e == 0 ? 0 : SYM ? sym_prefix(nc, nc, n_e) : (long long)nc * n;
+        const int qa = (int)((long long)group * n_raw / G), qb = (int)((long long)(group + 1) * n_raw / G);
         s_info[0] = n;
-        s_info[1] = ka;
-        s_info[2] = kb;
-        s_info[3] = q0;
+        s_info[1] = qa;
+        s_info[2] = qb;
         if (TMA) {
             for (int i = 0; i < ring; ++i) mbar_init(&s_bar[i], 1);
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         }
     }
     __syncthreads();
-    const int n_act = s_info[0], k_a = s_info[1], k_b = s_info[2], q0 = s_info[3];
-    const int n_stages = n_e == 0 ? 0 : SYM ? sym_prefix(k_b, nc, n_e) - q0 : (k_b - k_a) * n_act;
+    const int n_act = s_info[0], q0 = s_info[1], n_stages = s_info[2] - s_info[1];
 
-    const StageSpace sp{er, n_e, nc, n_act, k_a, q0, n_stages, s_tlist};
+    const StageSpace sp{er, n_e, nc, n_act, q0, n_stages, s_tlist};
     auto tx_of = [&](int j) { return stage_tx<SYM>(sp, j); };
     int n_live = 0, raw_next = 0;
     // Make entry `upto` of the compacted list exist while raw stages are left (all threads).
@@ -983,22 +995,36 @@ __global__ void __launch_bounds__(kThreads, 2) das_tiled_kernel(const __grid_con
     for (int p = 0; p < P; ++p) dst[p * kThreads + tid] = acc[p];
 }
 
-// Sum the chunk-group partials of every pixel in group order.
+// Sum the chunk-group partials of every pixel in group order.  With a
+// work-proportional schedule (tile_info != null) a tile's groups are the items
+// recorded in tile_info; a tile without items has no stage inside the record.
 template <int WCOL, int P>
-__global__ void das_reduce_kernel(const float* __restrict__ part, float* __restrict__ out, int nz,
-                                  int nx, int tiles_x, int tiles_z, int n_groups, int n_items) {
+__global__ void das_reduce_kernel(const float* __restrict__ part, const unsigned* __restrict__ tile_info,
+                                  float* __restrict__ out, int nz, int nx, int tiles_x, int tiles_z,
+                                  int n_groups, int n_items) {
     using S = Shape<WCOL, P>;
     const int ix = blockIdx.x * blockDim.x + threadIdx.x;
     const int iz = blockIdx.y;
     const int b = blockIdx.z;
     if (ix >= nx) return;
-    const int rank = tile_rank(iz / S::kRows, ix / S::kCols, tiles_z, tiles_x);
+    int first, groups;
+    if (tile_info) {
+        const unsigned info = tile_info[(iz / S::kRows) * tiles_x + ix / S::kCols];
+        first = (int)(info & 0xffffffu) - 1;
+        groups = (int)(info >> 24);
+        if (info == 0u) groups = 0;
+    } else {
+        first = tile_rank(iz / S::kRows, ix / S::kCols, tiles_z, tiles_x) * n_groups;
+        groups = n_groups;
+    }
     const int cl = ix % S::kCols, rl = iz % S::kRows;
     const int tid = (cl / WCOL) * 32 + (rl % S::kLR) * WCOL + (cl % WCOL);
     const int local = (rl / S::kLR) * kThreads + tid;
-    const float* p = part + ((long long)b * n_items + (long long)rank * n_groups) * (kThreads * P) + local;
     float s = 0.0f;
-    for (int k = 0; k < n_groups; ++k) s += p[(long long)k * (kThreads * P)];
+    if (groups > 0) {
+        const float* p = part + ((long long)b * n_items + first) * (kThreads * P) + local;
+        for (int k = 0; k < groups; ++k) s += p[(long long)k * (kThreads * P)];
+    }
     out[((long long)b * nz + iz) * nx + ix] = s;
 }
 
@@ -1070,9 +1096,12 @@ struct Cfg {
 struct Plan {
     Cfg cfg;
     int cols, rows;
-    int tiles_x, tiles_z, n_groups, n_items;
+    int tiles_x, tiles_z, n_groups, n_items;   // n_items: uniform groups, or the schedule's count
     int W, ring;
     bool tiled, db, tma, sym;
+    bool table;          // a work-proportional schedule fits (budget + tiles <= kMaxItems)
+    int budget;          // CTAs per frame the schedule aims for
+    size_t info_bytes;   // tile table in the workspace (after the status block)
     size_t smem;
     size_t ws_bytes;
 };
@@ -1085,11 +1114,14 @@ wf_status launch_tiled_v(DasArgs& A, const Plan& PL, int batch, cudaStream_t st)
     auto kern = das_tiled_kernel<MODE, T, WCOL, P, DB, TMA, CHECK, SYM>;
     wf_status s = ensure_smem_limit(kern, kMaxTiledSmem, smem_set);
     if (s != WF_OK) return s;
-    kern<<<dim3(PL.n_items, batch), kThreads, PL.smem, st>>>(A);
-    if ((s = last_launch_status()) != WF_OK) return s;
+    if (A.n_items > 0) {
+        kern<<<dim3(A.n_items, batch), kThreads, PL.smem, st>>>(A);
+        if ((s = last_launch_status()) != WF_OK) return s;
+    }
     dim3 rg((A.g.nx + 127) / 128, A.g.nz, batch);
-    das_reduce_kernel<WCOL, P><<<rg, 128, 0, st>>>(A.part, A.out, A.g.nz, A.g.nx, PL.tiles_x,
-                                                   PL.tiles_z, PL.n_groups, PL.n_items);
+    das_reduce_kernel<WCOL, P><<<rg, 128, 0, st>>>(A.part, A.use_table ? A.tile_info : nullptr, A.out,
+                                                   A.g.nz, A.g.nx, PL.tiles_x, PL.tiles_z, A.n_groups,
+                                                   A.n_items);
     return last_launch_status();
 }
 
