@@ -246,6 +246,20 @@ def oracle_sample(case, seconds, counts_px, start=0):
 
 # ----------------------------------------------------------------------------- native arm
 
+def max_over_ranks(value: float, world: int, device) -> float:
+    """The slowest rank's figure: replicas report the whole job's time as the max over ranks."""
+    if world <= 1:
+        return value
+    t = torch.tensor([value], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(frames_per_step: int, steps: int, world: int, ms_max: float) -> float:
+    """Whole-job frames/s of independent replicas: every rank's frames over the slowest time."""
+    return frames_per_step * steps * world / (ms_max / 1e3)
+
+
 def run_native(args, rank, world, local_rank):
     import paper_1811_01566_gb300 as wf
     from synth import configs  # noqa: F401
@@ -331,11 +345,7 @@ def run_native(args, rank, world, local_rank):
         e1.record(stream)
         barrier()
         clk.region(w0, time.time())
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
     clocks = clk.summary()
 
     # ---- stage split (eager, events between stages on the launching stream)
@@ -389,19 +399,14 @@ def run_native(args, rank, world, local_rank):
         db_host[cur].copy_(db, non_blocking=True)
     x1.record(stream)
     barrier()
-    e2e_ms = x0.elapsed_time(x1) / k3
+    e2e_ms = max_over_ranks(x0.elapsed_time(x1) / k3, world, dev)
     wall_e2e = (time.perf_counter() - t0) / k3 * 1e3
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
     wf.workspace_check(ws)
 
     if rank != 0:
         return None
     dense, active, contributing, per_px = delay_sum_counts(case, dev)
-    frames = args.steps * b * world
-    fps = frames / (ms / 1e3)
+    fps = replica_throughput(b, args.steps, world, ms)
     props = torch.cuda.get_device_properties(dev)
     peak_mhz = 2070.0
     try:
@@ -455,7 +460,7 @@ def run_native(args, rank, world, local_rank):
             "algorithmic": f"{FP32_OPS_PER_DELAY_SUM} FP32 ops x {contributing} contributing "
                            f"delay-sums per frame",
         },
-        "e2e": {"value": round(b / (e2e_ms / 1e3), 2), "unit": "frames/s",
+        "e2e": {"value": round(replica_throughput(b, 1, world, e2e_ms), 2), "unit": "frames/s",
                 "h2d_bytes_per_step": rf_bytes, "d2h_bytes_per_step": db.numel() * 4,
                 "wall_ms_per_step": round(wall_e2e, 4),
                 "pipelining": "next frame's pinned H2D copy on a copy stream overlaps the current "
