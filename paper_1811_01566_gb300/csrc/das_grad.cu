@@ -19,9 +19,17 @@
 // stage with global atomics (to both traces of a reciprocal pair).  Weight and
 // sound-speed sums are reduced per warp, per CTA and then globally.  Global
 // float atomics make the summation order (and so the last bits) run-dependent.
+#include <type_traits>
+
 #include "das_kernels.cuh"
 
 namespace wf {
+
+__device__ __forceinline__ f32x2 x2_mul(f32x2 a, f32x2 b) {
+    f32x2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
 
 constexpr int kBwdWCOL = 4;
 constexpr int kBwdP = 2;   // tile 32 x 16 pixels: three weight sets per chunk stay in registers
@@ -171,10 +179,17 @@ __global__ void __launch_bounds__(kThreads, 2) das_backward_kernel(const __grid_
     };
     need(0);
 
-    float Dr[kC][P], Wr[kC][P], Ar[kC][P], gR[kC];
+    // Per receive row c of the chunk, packed pixel pairs (2h, 2h + 1): distance Dr,
+    // weight Wr = a_r g_r and window Ar = a_r (PWI: both times the cotangent y, which
+    // does not depend on the transmit), and the weight-gradient partial gR.
+    static_assert(P % 2 == 0, "pixels per lane are processed in packed pairs");
+    constexpr int H = P / 2;
+    f32x2 Dr2[kC][H], Wr2[kC][H], Ar2[kC][H];
+    float gR[kC];
     float dr_min = 0.0f, dr_max = 0.0f, accC = 0.0f;
     unsigned cmask = 0u;
     RegStage<float, SYM> rs;
+    const f32x2 kMagic2 = x2_pack(kMagic, kMagic), scale2 = x2_pack(scale, scale);
     // Weight-gradient partials of the current chunk -> shared per-element sums.
     auto flush_chunk = [&](int r0c) {
         if (!NEED_PAR || cmask == 0u) return;
@@ -223,15 +238,24 @@ __global__ void __launch_bounds__(kThreads, 2) das_backward_kernel(const __grid_
                     const bool on = (cmask >> c) & 1u;
                     const Elem ee = el[(on ? r0 + c : r0) - er.x];
                     const float cc = elem_rel(ee, e0);
+                    float d[P], ar[P];
 #pragma unroll
                     for (int p = 0; p < P; ++p) {
-                        Dr[c][p] = on ? cc + dist_delta(ee, ux, kz[p]) : 0.0f;
-                        Ar[c][p] = on ? apod_w(g.apod, -(ee.ax + ux), kap[p]) : 0.0f;
-                        Wr[c][p] = Ar[c][p] * ee.g;
+                        d[p] = on ? cc + dist_delta(ee, ux, kz[p]) : 0.0f;
+                        ar[p] = on ? apod_w(g.apod, -(ee.ax + ux), kap[p]) : 0.0f;
                         if (on) {
-                            mn = fminf(mn, Dr[c][p]);
-                            mx = fmaxf(mx, Dr[c][p]);
+                            mn = fminf(mn, d[p]);
+                            mx = fmaxf(mx, d[p]);
                         }
+                    }
+#pragma unroll
+                    for (int p = 0; p < P; ++p)
+                        if (MODE == 1) ar[p] *= y[p];
+#pragma unroll
+                    for (int h = 0; h < H; ++h) {
+                        Dr2[c][h] = x2_pack(d[2 * h], d[2 * h + 1]);
+                        Ar2[c][h] = x2_pack(ar[2 * h], ar[2 * h + 1]);
+                        Wr2[c][h] = x2_pack(ar[2 * h] * ee.g, ar[2 * h + 1] * ee.g);
                     }
                 }
                 dr_min = warp_min(mn);
@@ -275,36 +299,76 @@ __global__ void __launch_bounds__(kThreads, 2) das_backward_kernel(const __grid_
         if (live) {
             const TxInfo& ti = a.tx[t];
             const float base_c = (float)si.lo + (ti.t0.hi + ti.t0.lo);   // s + base_c = path in samples
-            float gT = 0.0f;
+            const f32x2 base2 = x2_pack(base_c, base_c);
+            f32x2 tw2[H], yt2[H], ya2[H], gT2 = 0ull;
 #pragma unroll
-            for (int c = 0; c < kC; ++c) {
-                if (!((cm >> c) & 1u)) continue;
-                const float2* bc = buf + c * a.W;
-                int* gc = gw + c * GW;
+            for (int h = 0; h < H; ++h) {
+                tw2[h] = x2_pack(tw[2 * h], tw[2 * h + 1]);
+                yt2[h] = MODE == 0 ? x2_pack(yt[2 * h], yt[2 * h + 1]) : 0ull;
+                ya2[h] = MODE == 0 ? x2_pack(ya[2 * h], ya[2 * h + 1]) : 0ull;
+            }
+            // Per pixel pair and receive row: s = tw + Dr, i = floor(s), f = s - i,
+            // v = x[i] + f x'[i]; the RF cotangent y W (1 - f), y W f goes to window
+            // positions i, i + 1 in fixed point.  EDGE: the window crosses an end of
+            // the record, and terms without two recorded samples drop out (elsewhere
+            // every staged pair is inside the record).
+            auto terms = [&](auto edge_tag) {
+                constexpr bool EDGE = decltype(edge_tag)::value;
+                const unsigned lim = (unsigned)(a.ns - 2);
 #pragma unroll
-                for (int p = 0; p < P; ++p) {
-                    const float s = tw[p] + Dr[c][p];
-                    const float m = __fadd_rd(s, kMagic);
-                    const float f = s - (m - kMagic);
-                    const int idx = __float_as_int(m) - kMagicBits;
-                    const float2 ab = bc[idx];
-                    const float v = fmaf(f, ab.y, ab.x);
-                    const bool ok = (unsigned)(si.lo + idx) <= (unsigned)(a.ns - 2);
-                    const float yW = ok ? yt[p] * Wr[c][p] : 0.0f;
-                    if (NEED_RF && yW != 0.0f) {
-                        const float w1 = yW * f;
-                        atomicAdd(gc + idx, __float_as_int(fmaf(yW - w1, scale, kMagic)) - kMagicBits);
-                        atomicAdd(gc + idx + 1, __float_as_int(fmaf(w1, scale, kMagic)) - kMagicBits);
-                    }
-                    if (NEED_PAR) {
-                        accC = fmaf(yW * ab.y, base_c + s, accC);
-                        gR[c] = fmaf(yt[p] * Ar[c][p], v, gR[c]);
-                        if (MODE == 0) gT = fmaf(ya[p] * Wr[c][p], v, gT);
+                for (int c = 0; c < kC; ++c) {
+                    if (!((cm >> c) & 1u)) continue;
+                    const float2* bc = buf + c * a.W;
+                    int* gc = gw + c * GW;
+#pragma unroll
+                    for (int h = 0; h < H; ++h) {
+                        const f32x2 s2 = x2_add(tw2[h], Dr2[c][h]);
+                        const f32x2 m2 = x2_add_rm(s2, kMagic2);
+                        const f32x2 f2 = x2_sub(s2, x2_sub(m2, kMagic2));
+                        float m0, m1;
+                        x2_unpack(m2, m0, m1);
+                        const int i0 = __float_as_int(m0) - kMagicBits, i1 = __float_as_int(m1) - kMagicBits;
+                        const float2 a0 = bc[i0], a1 = bc[i1];
+                        float f0, f1;
+                        x2_unpack(f2, f0, f1);
+                        const float v0 = fmaf(f0, a0.y, a0.x), v1 = fmaf(f1, a1.y, a1.x);
+                        f32x2 yW2 = MODE == 0 ? x2_mul(yt2[h], Wr2[c][h]) : Wr2[c][h];
+                        if (EDGE) {
+                            float y0, y1;
+                            x2_unpack(yW2, y0, y1);
+                            if ((unsigned)(si.lo + i0) > lim) y0 = 0.0f;
+                            if ((unsigned)(si.lo + i1) > lim) y1 = 0.0f;
+                            yW2 = x2_pack(y0, y1);
+                        }
+                        if (NEED_RF) {
+                            const f32x2 w12 = x2_mul(yW2, f2);
+                            float q0, q1, q2, q3;
+                            x2_unpack(x2_fma(x2_sub(yW2, w12), scale2, kMagic2), q0, q1);
+                            x2_unpack(x2_fma(w12, scale2, kMagic2), q2, q3);
+                            atomicAdd(gc + i0, __float_as_int(q0) - kMagicBits);
+                            atomicAdd(gc + i0 + 1, __float_as_int(q2) - kMagicBits);
+                            atomicAdd(gc + i1, __float_as_int(q1) - kMagicBits);
+                            atomicAdd(gc + i1 + 1, __float_as_int(q3) - kMagicBits);
+                        }
+                        if (NEED_PAR) {
+                            // sound speed: y W x'[i] (s + base); receive weights: y w_t a_r v;
+                            // transmit weight (STAI): y a_t W_r v
+                            float p0, p1, g0, g1;
+                            x2_unpack(x2_mul(yW2, x2_add(base2, s2)), p0, p1);
+                            accC = fmaf(p0, a0.y, fmaf(p1, a1.y, accC));
+                            x2_unpack(MODE == 0 ? x2_mul(yt2[h], Ar2[c][h]) : Ar2[c][h], g0, g1);
+                            gR[c] = fmaf(g0, v0, fmaf(g1, v1, gR[c]));
+                            if (MODE == 0) gT2 = x2_fma(x2_mul(ya2[h], Wr2[c][h]), x2_pack(v0, v1), gT2);
+                        }
                     }
                 }
-            }
+            };
+            if (si.edge()) terms(std::true_type{});
+            else terms(std::false_type{});
             if (NEED_PAR && MODE == 0) {
-                gT = warp_sum(gT);
+                float g0, g1;
+                x2_unpack(gT2, g0, g1);
+                const float gT = warp_sum(g0 + g1);
                 if (lane == 0 && gT != 0.0f) atomicAdd(&ge[a.tx[t].e - er.x], gT);
             }
         }

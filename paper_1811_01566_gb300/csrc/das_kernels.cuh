@@ -822,12 +822,16 @@ __global__ void __launch_bounds__(kThreads, 2) das_tiled_kernel(const __grid_con
         if (TMA) {
             stuck = !mbar_wait_bounded(&s_bar[q % ring], (unsigned)((q / ring) & 1));
             if (!stuck) {
-                // raw slot -> FP32 pairs, segment (trace c, block kk) = (tid >> 6 [+4], tid & 63)
+                // raw slot -> FP32 pairs, 8-sample segment kk of trace row c.  Reciprocal
+                // STAI (two traces per row): row c = warp, kk = lane [+ 32], so every warp
+                // takes an equal share; otherwise (c, kk) = (tid >> 6 [+ 4], tid & 63).
+                static_assert(kThreads / 32 == kC, "one staged trace row per warp");
                 const T* slot = raw + (size_t)(q % ring) * kRawRows * RW;
-                const int nseg = si.len >> 3, kk = tid & 63;
+                const int nseg = si.len >> 3;
 #pragma unroll
                 for (int i = 0; i < 2; ++i) {
-                    const int c = (tid >> 6) + 4 * i;
+                    const int c = SYM ? warp : (tid >> 6) + 4 * i;
+                    const int kk = SYM ? lane + 32 * i : tid & 63;
                     if (kk >= nseg) continue;
                     float2* dst = buf + c * a.W + 8 * kk;
                     const bool on = r0 + c <= r_last && (!SYM || r0 + c >= t);
@@ -949,7 +953,8 @@ __global__ void __launch_bounds__(kThreads, 2) das_tiled_kernel(const __grid_con
         if (live) {
             // Per pixel: s = tw + Dr, i = floor(s) by the round-down add of 1.5 * 2^23,
             // f = s - i, v = x[i] + f (x[i+1] - x[i]), acc += Wr v -- two pixels per
-            // packed instruction.
+            // packed instruction (the interpolation itself in scalar FMAs, which read
+            // the gathered pairs where they landed).
             f32x2 tw2[H], acct2[H];
 #pragma unroll
             for (int h = 0; h < H; ++h) {
@@ -974,7 +979,9 @@ __global__ void __launch_bounds__(kThreads, 2) das_tiled_kernel(const __grid_con
                         i1 = 0;
                     }
                     const float2 a0 = bc[i0], a1 = bc[i1];
-                    const f32x2 v2 = x2_fma(f2, x2_pack(a0.y, a1.y), x2_pack(a0.x, a1.x));
+                    float f0, f1;
+                    x2_unpack(f2, f0, f1);
+                    const f32x2 v2 = x2_pack(fmaf(f0, a0.y, a0.x), fmaf(f1, a1.y, a1.x));
                     acct2[h] = x2_fma(Wr2[c][h], v2, acct2[h]);
                 }
             }
