@@ -170,6 +170,51 @@ wf_status wf_das_delays(const wf_probe* probe, const wf_grid* grid, int32_t mode
                         float* out_rel, wf_stream stream);
 
 /*
+ * RF transfer plan.  A box [t0, t1) x [r0, r1) x [s0, s1) of the
+ * [n_tx][n_rx][n_samples] RF array of one frame.
+ */
+typedef struct {
+    int32_t t0, t1, r0, r1, s0, s1;
+} wf_rf_box;
+
+/*
+ * Boxes that together hold every sample wf_das_stai (mode 0) / wf_das_pwi
+ * (mode 1) can read for these arguments: the staging windows of the tiled
+ * kernels (Sec. II-B's per-element delays bounded over each pixel tile, every
+ * tile configuration and pairing a call may select, with slack for the FP32
+ * bounds) -- or whole traces where a grid sends the call to the per-pixel
+ * path.  Samples outside the boxes never reach any result, so copying only the
+ * boxes of a frame into the device RF buffer gives bit-identical images.  Host
+ * computation only (no CUDA call); plan once per geometry.
+ *
+ *  mode, n_tx, tx_elem, angles_rad, t_start   as wf_das_delays (host arrays)
+ *  n_rx, n_samples, dtype                     as wf_das_stai
+ *  group        transmits per box (>= 1): one box per group of consecutive
+ *               transmits, over the group's receive and sample hull
+ *  boxes        host array of max_boxes entries, or NULL with max_boxes = 0
+ *               to query the count
+ *  n_boxes      receives the number of boxes; WF_ERR_INVALID_ARG (count still
+ *               set) when it exceeds a non-zero max_boxes
+ */
+wf_status wf_das_rf_boxes(const wf_probe* probe, const wf_grid* grid, int32_t mode,
+                          int32_t n_tx, const int32_t* tx_elem, const double* angles_rad,
+                          const double* t_start, int32_t n_rx, int32_t n_samples,
+                          wf_dtype dtype, int32_t group, wf_rf_box* boxes, int32_t max_boxes,
+                          int32_t* n_boxes);
+
+/*
+ * Copy the boxes of one [n_tx][n_rx][n_samples] RF frame from src to dst
+ * (same layout; one 3D copy per box, direction inferred from the pointers:
+ * pinned host to device for the end-to-end path).  Asynchronous on stream.
+ *
+ *  elem_bytes   2 (int16 / float16) or 4 (float32)
+ *  boxes        host array of n_boxes boxes inside the array's bounds
+ */
+wf_status wf_copy_rf_boxes(const void* src, void* dst, int32_t n_tx, int32_t n_rx,
+                           int32_t n_samples, int32_t elem_bytes, const wf_rf_box* boxes,
+                           int32_t n_boxes, wf_stream stream);
+
+/*
  * Reverse-mode delay-and-sum (a differentiable beamformer: DAS inside a
  * learned pipeline, the use Sec. I and Sec. IV of the paper point to).  For a
  * cotangent y = grad_out of the beamformed image b of wf_das_stai (mode 0) or

@@ -24,7 +24,8 @@ from . import _build
 __all__ = ["Probe", "Grid", "WfError", "HANN", "RECT", "NONE", "das_stai", "das_pwi",
            "das_workspace_bytes", "das_delays", "das_backward", "das", "envelope", "logclip",
            "envelope_backward", "logclip_backward", "bmode", "bmode_diff", "fir", "iq_demod",
-           "fir_bandpass", "workspace_check", "library_path", "version"]
+           "fir_bandpass", "workspace_check", "rf_boxes", "copy_rf_boxes", "library_path",
+           "version"]
 
 HANN, RECT, NONE = 0, 1, 2
 _DTYPES = {torch.float32: 0, torch.float16: 1, torch.int16: 2}
@@ -49,6 +50,10 @@ class _WfProbe(C.Structure):
 class _WfGrid(C.Structure):
     _fields_ = [("nz", C.c_int32), ("nx", C.c_int32), ("x_min", C.c_double),
                 ("x_max", C.c_double), ("z_min", C.c_double), ("z_max", C.c_double)]
+
+
+class _WfRfBox(C.Structure):
+    _fields_ = [(n, C.c_int32) for n in ("t0", "t1", "r0", "r1", "s0", "s1")]
 
 
 _lib = None
@@ -98,6 +103,11 @@ def _load():
             lib.wf_iq_demod.restype = C.c_int
             lib.wf_fir_bandpass.argtypes = [f64, f64, f64, i32, C.POINTER(C.c_float)]
             lib.wf_fir_bandpass.restype = C.c_int
+            lib.wf_das_rf_boxes.argtypes = [P, G, i32, i32, vp, vp, vp, i32, i32, i32, i32, vp, i32,
+                                            C.POINTER(i32)]
+            lib.wf_das_rf_boxes.restype = C.c_int
+            lib.wf_copy_rf_boxes.argtypes = [vp, vp, i32, i32, i32, i32, vp, i32, vp]
+            lib.wf_copy_rf_boxes.restype = C.c_int
             lib.wf_workspace_check.argtypes = [vp, sz, vp]
             lib.wf_workspace_check.restype = C.c_int
             lib.wf_status_string.argtypes = [C.c_int]
@@ -244,6 +254,63 @@ def das_delays(probe: Probe, grid: Grid, mode: str, pix: torch.Tensor, *, n_tx: 
                                rel.data_ptr(), _stream(stream))
     _check(st, "wf_das_delays")
     return lo.cpu().double() + rel.cpu().double()
+
+
+def _scan_args(mode: str, n_tx: int, tx_elem, angles, t_start):
+    tx = None if tx_elem is None else (C.c_int32 * n_tx)(*[int(v) for v in tx_elem])
+    ang = None if angles is None else (C.c_double * n_tx)(*[float(v) for v in angles])
+    if t_start is None:
+        ts = None
+    else:
+        vals = [float(t_start)] if mode == "stai" and not hasattr(t_start, "__len__") else \
+            [float(v) for v in t_start]
+        ts = (C.c_double * len(vals))(*vals)
+    return tx, ang, ts
+
+
+def rf_boxes(probe: Probe, grid: Grid, mode: str, *, n_tx: int, n_samples: int,
+             dtype: torch.dtype = torch.int16, tx_elem=None, angles=None, t_start=None,
+             group: int = 16) -> list[tuple[int, int, int, int, int, int]]:
+    """Transfer plan of one RF frame: boxes (t0, t1, r0, r1, s0, s1) of the [n_tx][n_elements]
+    [n_samples] array holding every sample ``das_stai`` / ``das_pwi`` with these arguments can
+    read (one box per ``group`` consecutive transmits).  Host computation; plan once per scan."""
+    if mode not in ("stai", "pwi"):
+        raise ValueError("mode must be 'stai' or 'pwi'")
+    if dtype not in _DTYPES:
+        raise ValueError("dtype must be float32, float16 or int16")
+    tx, ang, ts = _scan_args(mode, n_tx, tx_elem, angles, t_start)
+    lib = _load()
+    n = C.c_int32(0)
+    args = (C.byref(probe._c()), C.byref(grid._c()), 0 if mode == "stai" else 1, int(n_tx), tx, ang,
+            ts, probe.n_elements, int(n_samples), _DTYPES[dtype], int(group))
+    _check(lib.wf_das_rf_boxes(*args, None, 0, C.byref(n)), "wf_das_rf_boxes")
+    if n.value == 0:
+        return []
+    arr = (_WfRfBox * n.value)()
+    _check(lib.wf_das_rf_boxes(*args, arr, n.value, C.byref(n)), "wf_das_rf_boxes")
+    return [(b.t0, b.t1, b.r0, b.r1, b.s0, b.s1) for b in arr]
+
+
+def copy_rf_boxes(src: torch.Tensor, dst: torch.Tensor, boxes, stream=None) -> None:
+    """Copy the boxes of one RF frame [n_tx, n_rx, n_samples] from ``src`` (pinned host or CUDA)
+    into ``dst`` (CUDA, same shape and dtype), asynchronously on ``stream``."""
+    if src.dim() == 4 and src.shape[0] == 1:
+        src = src[0]
+    if dst.dim() == 4 and dst.shape[0] == 1:
+        dst = dst[0]
+    if src.shape != dst.shape or src.dim() != 3 or src.dtype != dst.dtype:
+        raise ValueError("src and dst must be [n_tx, n_rx, n_samples] frames of one dtype")
+    if not (dst.is_cuda and src.is_contiguous() and dst.is_contiguous()):
+        raise ValueError("dst must be a contiguous CUDA tensor and src contiguous")
+    if not (src.is_cuda or src.is_pinned()):
+        raise ValueError("src must be pinned host memory or a CUDA tensor")
+    if src.element_size() not in (2, 4):
+        raise ValueError("RF elements must be 2 or 4 bytes")
+    arr = (_WfRfBox * len(boxes))(*[_WfRfBox(*map(int, b)) for b in boxes])
+    n_tx, n_rx, ns = src.shape
+    _check(_load().wf_copy_rf_boxes(src.data_ptr(), dst.data_ptr(), n_tx, n_rx, ns,
+                                    src.element_size(), arr, len(boxes), _stream(stream)),
+           "wf_copy_rf_boxes")
 
 
 def das_backward(rf: torch.Tensor, grad_out: torch.Tensor, probe: Probe, grid: Grid, mode: str, *,

@@ -452,10 +452,210 @@ double fill_tx(DasArgs& a, const wf_probe* probe, int mode, int n_tx, const int3
     return extra;
 }
 
+// Bounds over the tile rectangle [xlo, xhi] x [zlo, zhi] (samples) of the path of one
+// (transmit, receive element) pair before the transmit offset, in double: the same
+// convex-bound argument as the kernels' window planning (maximum on a bottom corner,
+// minimum on the top edge at the clamped stationary point).
+void pair_bounds_d(int mode, const GeomD& D, const TxInfo& ti, int e_t, int r, double xlo,
+                   double xhi, double zlo, double zhi, double& mn, double& mx) {
+    const double xr = D.xe0 + r * D.pitch;
+    if (mode == 0) {
+        const double xt = D.xe0 + e_t * D.pitch;
+        const double xm = std::min(std::max(0.5 * (xt + xr), xlo), xhi);
+        mn = std::hypot(xm - xt, zlo) + std::hypot(xm - xr, zlo);
+        mx = std::max(std::hypot(xlo - xt, zhi) + std::hypot(xlo - xr, zhi),
+                      std::hypot(xhi - xt, zhi) + std::hypot(xhi - xr, zhi));
+        return;
+    }
+    const double sn = (double)ti.sin.hi + ti.sin.lo, cs = (double)ti.cos.hi + ti.cos.lo;
+    const double xm = std::min(std::max(xr - zlo * sn / cs, xlo), xhi);
+    mn = xm * sn + zlo * cs + std::hypot(xm - xr, zlo);
+    mx = std::max(xlo * sn + zhi * cs + std::hypot(xlo - xr, zhi),
+                  xhi * sn + zhi * cs + std::hypot(xhi - xr, zhi));
+}
+
+// Hull [lo, hi) over the whole frame of the samples the DAS kernels may stage
+// from each trace [t][r] (lo >= hi: none), for every tile configuration, staging
+// path and pairing a call with these arguments can select.  A superset by
+// construction: element ranges one element wider than the kernels', every
+// receive-chunk mate within 7 elements (for STAI also on the transmit side, which
+// the reciprocal pairing stages from either end), and 24 / 32 samples of slack
+// below / above the double-precision bounds for the kernels' FP32 bounds, their
+// +-2 margins, 8-sample alignment and trailing neighbour segment.  A grid that
+// sends a call to the per-pixel fallback needs whole traces.
+void staged_hulls(int mode, const wf_probe* p, const wf_grid* g, const DasArgs& a, int n_tx,
+                  const int32_t* tx_elem, int ns, int rf_bytes, std::vector<int>& lo,
+                  std::vector<int>& hi) {
+    const int E = p->n_elements;
+    lo.assign((size_t)n_tx * E, ns);
+    hi.assign((size_t)n_tx * E, 0);
+    Geom G;
+    GeomD D;
+    make_geom(p, g, G, D);
+    const bool sym_possible = mode == 0 && n_tx == E &&
+                              [&] { for (int t = 0; t < n_tx; ++t) if ((tx_elem ? tx_elem[t] : t) != t) return false;
+                                    return true; }();
+    const Cfg* cfgs = mode == 0 ? kStaiCfgs : kPwiCfgs;
+    std::vector<Cfg> tiled;
+    for (int sym = 0; sym <= (sym_possible ? 1 : 0); ++sym) {
+        bool any = false;
+        for (int i = 0; i < 2; ++i)
+            if (plan_for(mode, cfgs[i], D, p, g, 1, n_tx, ns, rf_bytes, sym == 1).tiled) {
+                any = true;
+                if (std::find_if(tiled.begin(), tiled.end(), [&](const Cfg& c) {
+                        return c.wcol == cfgs[i].wcol && c.p == cfgs[i].p; }) == tiled.end())
+                    tiled.push_back(cfgs[i]);
+            }
+        if (!any) {   // the per-pixel fallback may read any sample
+            std::fill(lo.begin(), lo.end(), 0);
+            std::fill(hi.begin(), hi.end(), ns);
+            return;
+        }
+    }
+    const double two_f = 2.0 * (p->apod == WF_APOD_NONE ? 1.0 : p->f_number);
+    constexpr int kMate = kC - 1;
+    std::vector<double> bmn, bmx, rmn, rmx;
+    for (const Cfg& cfg : tiled) {
+        const int cols = 8 * cfg.wcol, rows = (32 / cfg.wcol) * cfg.p;
+        const int tiles_x = (g->nx + cols - 1) / cols, tiles_z = (g->nz + rows - 1) / rows;
+        for (int tz = 0; tz < tiles_z; ++tz)
+            for (int tx = 0; tx < tiles_x; ++tx) {
+                const double xlo = D.gx0 + (double)(tx * cols) * D.gdx;
+                const double xhi = D.gx0 + (double)(tx * cols + cols - 1) * D.gdx;
+                const double zlo = D.gz0 + (double)(tz * rows) * D.gdz;
+                const double zhi = D.gz0 + (double)(tz * rows + rows - 1) * D.gdz;
+                int elo = 0, ehi = E - 1;
+                if (p->apod != WF_APOD_NONE) {
+                    if (!(zhi > 0.0)) continue;
+                    const double half = zhi / two_f;
+                    elo = std::max(0, (int)std::floor((xlo - half - D.xe0) / D.pitch) - 2);
+                    ehi = std::min(E - 1, (int)std::ceil((xhi + half - D.xe0) / D.pitch) + 2);
+                    if (elo > ehi) continue;
+                }
+                const int n_e = ehi - elo + 1;
+                // transmit sides: elements (STAI, [n_e]) or angles (PWI, [n_tx]); bounds [side][receive]
+                const int n_side = mode == 0 ? n_e : n_tx;
+                bmn.assign((size_t)n_side * n_e, 0.0);
+                bmx.assign((size_t)n_side * n_e, 0.0);
+                for (int u = 0; u < n_side; ++u)
+                    for (int r = 0; r < n_e; ++r)
+                        pair_bounds_d(mode, D, a.tx[mode == 0 ? 0 : u], elo + u, elo + r, xlo, xhi, zlo,
+                                      zhi, bmn[(size_t)u * n_e + r], bmx[(size_t)u * n_e + r]);
+                // receive-chunk mates within kMate elements
+                rmn.assign(bmn.size(), 0.0);
+                rmx.assign(bmx.size(), 0.0);
+                for (int u = 0; u < n_side; ++u)
+                    for (int r = 0; r < n_e; ++r) {
+                        double m0 = 1e300, m1 = -1e300;
+                        for (int q = std::max(0, r - kMate); q <= std::min(n_e - 1, r + kMate); ++q) {
+                            m0 = std::min(m0, bmn[(size_t)u * n_e + q]);
+                            m1 = std::max(m1, bmx[(size_t)u * n_e + q]);
+                        }
+                        rmn[(size_t)u * n_e + r] = m0;
+                        rmx[(size_t)u * n_e + r] = m1;
+                    }
+                for (int t = 0; t < n_tx; ++t) {
+                    const int e_t = mode == 0 ? (tx_elem ? tx_elem[t] : t) : -1;
+                    if (mode == 0 && (e_t < elo || e_t > ehi)) continue;
+                    const double t0 = (double)a.tx[t].t0.hi + a.tx[t].t0.lo;
+                    // STAI: transmit-side mates too when the reciprocal pairing can apply
+                    const int u0 = mode == 0 ? (sym_possible ? std::max(0, e_t - elo - kMate) : e_t - elo) : t;
+                    const int u1 = mode == 0 ? (sym_possible ? std::min(n_e - 1, e_t - elo + kMate) : e_t - elo) : t;
+                    for (int r = 0; r < n_e; ++r) {
+                        double m0 = 1e300, m1 = -1e300;
+                        for (int u = u0; u <= u1; ++u) {
+                            m0 = std::min(m0, rmn[(size_t)u * n_e + r]);
+                            m1 = std::max(m1, rmx[(size_t)u * n_e + r]);
+                        }
+                        const double a0 = std::floor(m0 - t0) - 24.0, a1 = std::ceil(m1 - t0) + 32.0;
+                        const int s0 = (int)std::max(0.0, std::min((double)ns, a0));
+                        const int s1 = (int)std::max(0.0, std::min((double)ns, a1));
+                        if (s0 >= s1) continue;
+                        const size_t k = (size_t)t * E + elo + r;
+                        lo[k] = std::min(lo[k], s0);
+                        hi[k] = std::max(hi[k], s1);
+                    }
+                }
+            }
+    }
+}
+
 }  // namespace
 }  // namespace wf
 
 using namespace wf;
+
+extern "C" wf_status wf_das_rf_boxes(const wf_probe* probe, const wf_grid* grid, int32_t mode,
+                                     int32_t n_tx, const int32_t* tx_elem, const double* angles_rad,
+                                     const double* t_start, int32_t n_rx, int32_t n_samples,
+                                     wf_dtype dtype, int32_t group, wf_rf_box* boxes,
+                                     int32_t max_boxes, int32_t* n_boxes) {
+    thread_local DasArgs local;
+    DasArgs& a = local;
+    wf_status s = check_probe_grid(probe, grid);
+    if (s != WF_OK) return s;
+    if (mode != 0 && mode != 1) return WF_ERR_INVALID_ARG;
+    if (mode == 1 && !angles_rad) return WF_ERR_INVALID_ARG;
+    if (n_tx < 1 || n_tx > WF_MAX_TX || n_rx != probe->n_elements) return WF_ERR_INVALID_ARG;
+    if (n_samples < 1 || n_samples > WF_MAX_SAMPLES || group < 1 || !n_boxes) return WF_ERR_INVALID_ARG;
+    if (dtype != WF_F32 && dtype != WF_F16 && dtype != WF_I16) return WF_ERR_INVALID_ARG;
+    if (max_boxes < 0 || (max_boxes > 0 && !boxes)) return WF_ERR_INVALID_ARG;
+    if (fill_tx(a, probe, mode, n_tx, tx_elem, angles_rad, t_start, mode == 1) < 0.0) return WF_ERR_INVALID_ARG;
+    std::vector<int> lo, hi;
+    staged_hulls(mode, probe, grid, a, n_tx, tx_elem, n_samples, dtype == WF_F32 ? 4 : 2, lo, hi);
+    const int E = probe->n_elements;
+    int n = 0;
+    for (int t0 = 0; t0 < n_tx; t0 += group) {
+        const int t1 = std::min(n_tx, t0 + group);
+        int r0 = E, r1 = -1, s0 = n_samples, s1 = 0;
+        for (int t = t0; t < t1; ++t)
+            for (int r = 0; r < E; ++r) {
+                const size_t k = (size_t)t * E + r;
+                if (lo[k] >= hi[k]) continue;
+                r0 = std::min(r0, r);
+                r1 = std::max(r1, r);
+                s0 = std::min(s0, lo[k]);
+                s1 = std::max(s1, hi[k]);
+            }
+        if (r1 < r0) continue;
+        s0 &= ~7;                                        // 8-sample (16-byte for 16-bit RF) ends
+        s1 = std::min(n_samples, (s1 + 7) & ~7);
+        if (n < max_boxes) boxes[n] = wf_rf_box{t0, t1, r0, r1 + 1, s0, s1};
+        ++n;
+    }
+    *n_boxes = n;
+    return n > max_boxes && max_boxes > 0 ? WF_ERR_INVALID_ARG : WF_OK;
+}
+
+extern "C" wf_status wf_copy_rf_boxes(const void* src, void* dst, int32_t n_tx, int32_t n_rx,
+                                      int32_t n_samples, int32_t elem_bytes, const wf_rf_box* boxes,
+                                      int32_t n_boxes, wf_stream stream) {
+    if (!src || !dst || n_tx < 1 || n_rx < 1 || n_samples < 1 || n_boxes < 0 || (n_boxes > 0 && !boxes))
+        return WF_ERR_INVALID_ARG;
+    if (elem_bytes != 2 && elem_bytes != 4) return WF_ERR_INVALID_ARG;
+    for (int i = 0; i < n_boxes; ++i) {
+        const wf_rf_box& b = boxes[i];
+        if (b.t0 < 0 || b.t1 > n_tx || b.t0 >= b.t1 || b.r0 < 0 || b.r1 > n_rx || b.r0 >= b.r1 ||
+            b.s0 < 0 || b.s1 > n_samples || b.s0 >= b.s1)
+            return WF_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const size_t pitch = (size_t)n_samples * elem_bytes;
+    for (int i = 0; i < n_boxes; ++i) {
+        const wf_rf_box& b = boxes[i];
+        cudaMemcpy3DParms P{};
+        P.srcPtr = make_cudaPitchedPtr(const_cast<void*>(src), pitch, pitch, (size_t)n_rx);
+        P.dstPtr = make_cudaPitchedPtr(dst, pitch, pitch, (size_t)n_rx);
+        P.srcPos = make_cudaPos((size_t)b.s0 * elem_bytes, (size_t)b.r0, (size_t)b.t0);
+        P.dstPos = P.srcPos;
+        P.extent = make_cudaExtent((size_t)(b.s1 - b.s0) * elem_bytes, (size_t)(b.r1 - b.r0),
+                                   (size_t)(b.t1 - b.t0));
+        P.kind = cudaMemcpyDefault;
+        const wf_status s = cuda_status(cudaMemcpy3DAsync(&P, st));
+        if (s != WF_OK) return s;
+    }
+    return WF_OK;
+}
 
 extern "C" size_t wf_das_workspace_bytes(const wf_probe* probe, const wf_grid* grid, int32_t batch,
                                          int32_t n_tx) {

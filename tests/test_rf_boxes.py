@@ -1,0 +1,178 @@
+"""RF transfer plan (wf_das_rf_boxes / wf_copy_rf_boxes).
+
+CPU: the boxes hold every sample pair (i, i + 1) that a contributing term of
+the DAS sum (Sec. II-B: delay from the paper's geometry, weight inside the
+f-number aperture, i inside the record) interpolates, for STAI with every
+element firing (reciprocal pairing), STAI on a transmit subset, PWI, a
+non-zero t_start and every apodization; boxes stay inside the array; coarse
+grids that go to the per-pixel path get whole traces.  The delays here are
+the paper's formulas in float64, independent of the planner's tile bounds.
+
+GPU: DAS on a device buffer that received only the boxes (everything else
+poisoned: NaN for float RF, which any staged-but-missing sample would carry
+into the image through a zero weight) is bit-identical to DAS on the full
+frame.
+"""
+import numpy as np
+import pytest
+import torch
+
+import paper_1811_01566_gb300 as wf
+from synth import configs
+
+
+def _probe_grid(case):
+    pr = wf.Probe(case.n_elements, case.pitch, case.fs, case.c, case.f_number, case.apod)
+    gr = wf.Grid(case.nz, case.nx, case.x_min, case.x_max, case.z_min, case.z_max)
+    return pr, gr
+
+
+def _boxes(case, group):
+    pr, gr = _probe_grid(case)
+    if case.mode == "stai":
+        return wf.rf_boxes(pr, gr, "stai", n_tx=case.n_tx, n_samples=case.n_samples,
+                           tx_elem=case.tx_elem, t_start=case.t_start, group=group)
+    return wf.rf_boxes(pr, gr, "pwi", n_tx=case.n_tx, n_samples=case.n_samples,
+                       angles=case.angles, t_start=case.t_starts, group=group)
+
+
+def _used_samples(case):
+    """Boolean [n_tx][E][ns]: samples some contributing term interpolates (i and i + 1)."""
+    E, ns = case.n_elements, case.n_samples
+    xe = (np.arange(E) - 0.5 * (E - 1)) * case.pitch
+    x = np.linspace(case.x_min, case.x_max, case.nx)
+    z = np.linspace(case.z_min, case.z_max, case.nz)
+    px, pz = [a.ravel() for a in np.meshgrid(x, z)]
+    dist = np.sqrt((px[:, None] - xe[None, :]) ** 2 + pz[:, None] ** 2)          # [pix, E]
+    if case.apod == wf.NONE:
+        inside = np.ones_like(dist, dtype=bool)
+    else:
+        inside = np.abs(xe[None, :] - px[:, None]) < pz[:, None] / (2.0 * case.f_number)
+    sc = case.fs / case.c
+    used = np.zeros((case.n_tx, E, ns), dtype=bool)
+    for t in range(case.n_tx):
+        if case.mode == "stai":
+            e = int(case.tx_elem[t])
+            s = (dist[:, e:e + 1] + dist) * sc - case.t_start * case.fs
+            w = inside[:, e:e + 1] & inside
+        else:
+            th = case.angles[t]
+            s = ((px * np.sin(th) + pz * np.cos(th))[:, None] + dist) * sc - case.t_starts[t] * case.fs
+            w = inside
+        i = np.floor(s).astype(np.int64)
+        ok = w & (i >= 0) & (i <= ns - 2)
+        rr = np.broadcast_to(np.arange(E)[None, :], i.shape)[ok]
+        ii = i[ok]
+        used[t, rr, ii] = True
+        used[t, rr, ii + 1] = True
+    return used
+
+
+def _covered(case, boxes):
+    cov = np.zeros((case.n_tx, case.n_elements, case.n_samples), dtype=bool)
+    for t0, t1, r0, r1, s0, s1 in boxes:
+        cov[t0:t1, r0:r1, s0:s1] = True
+    return cov
+
+
+CASES = {
+    "stai_reciprocal": dict(mode="stai", seed=1, n_elements=32, n_tx=32, n_samples=1024, nz=96, nx=48),
+    "stai_subset": dict(mode="stai", seed=2, n_elements=40, n_tx=10, n_samples=900, nz=64, nx=40),
+    "stai_t_start": dict(mode="stai", seed=3, n_elements=24, n_tx=24, n_samples=800, nz=64, nx=32,
+                         t_start=1.5e-6),
+    "stai_rect": dict(mode="stai", seed=4, n_elements=24, n_tx=24, n_samples=800, nz=50, nx=30,
+                      apod=wf.RECT),
+    "stai_no_apod": dict(mode="stai", seed=5, n_elements=16, n_tx=16, n_samples=700, nz=40, nx=24,
+                         apod=wf.NONE),
+    "pwi": dict(mode="pwi", seed=6, n_elements=32, n_tx=7, n_samples=1200, nz=96, nx=48, t_start=1.0),
+    "pwi_deep": dict(mode="pwi", seed=7, n_elements=48, n_tx=5, n_samples=640, nz=80, nx=40,
+                     z_range=(5e-3, 30e-3)),
+}
+
+
+@pytest.mark.parametrize("group", [1, 4, 16])
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_boxes_hold_every_interpolated_sample(name, group):
+    case = configs.random_case(**CASES[name])
+    boxes = _boxes(case, group)
+    used = _used_samples(case)
+    assert used.any()
+    missing = used & ~_covered(case, boxes)
+    assert not missing.any(), (name, np.argwhere(missing)[:5])
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_boxes_in_bounds_and_ordered(name):
+    case = configs.random_case(**CASES[name])
+    boxes = _boxes(case, 4)
+    prev = 0
+    for t0, t1, r0, r1, s0, s1 in boxes:
+        assert prev <= t0 < t1 <= case.n_tx and t1 - t0 <= 4
+        assert 0 <= r0 < r1 <= case.n_elements
+        assert 0 <= s0 < s1 <= case.n_samples and s0 % 8 == 0
+        assert s1 % 8 == 0 or s1 == case.n_samples
+        prev = t1
+
+
+def test_boxes_skip_what_the_record_never_reaches():
+    """A deep full STAI scan: the plan leaves out samples before the shallowest path and
+    element pairs that share no pixel's aperture."""
+    case = configs.random_case("stai", 8, n_elements=64, n_tx=64, n_samples=1024, nz=512, nx=128,
+                               z_range=(5e-3, 40e-3))
+    boxes = _boxes(case, 1)
+    vol = sum((t1 - t0) * (r1 - r0) * (s1 - s0) for t0, t1, r0, r1, s0, s1 in boxes)
+    assert vol < 0.9 * case.n_tx * case.n_elements * case.n_samples
+    assert min(b[4] for b in boxes) > 0
+
+
+def test_coarse_grid_takes_whole_traces():
+    """Windows beyond the tiled kernels' limit send the call to the per-pixel path, which may
+    read any sample: every trace is planned whole."""
+    case = configs.random_case("pwi", 9, n_elements=16, n_tx=3, n_samples=512, nz=8, nx=8,
+                               z_range=(1e-3, 60e-3))
+    boxes = _boxes(case, 3)
+    assert boxes == [(0, 3, 0, 16, 0, 512)]
+
+
+def test_box_query_and_errors():
+    case = configs.random_case(**CASES["pwi"])
+    pr, gr = _probe_grid(case)
+    with pytest.raises(ValueError):
+        wf.rf_boxes(pr, gr, "xyz", n_tx=3, n_samples=64)
+    with pytest.raises(wf.WfError):
+        wf.rf_boxes(pr, gr, "pwi", n_tx=3, n_samples=64, angles=[0.0, 0.1, 0.2], group=0)
+    with pytest.raises(wf.WfError):   # angles missing
+        wf.rf_boxes(pr, gr, "pwi", n_tx=3, n_samples=64)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("name,dtype", [("stai_reciprocal", "f32"), ("stai_reciprocal", "i16"),
+                                        ("stai_subset", "f32"), ("pwi", "f32"), ("pwi_deep", "f16")])
+def test_das_from_boxes_is_bit_identical(name, dtype):
+    case = configs.random_case(**CASES[name], dtype=dtype)
+    pr, gr = _probe_grid(case)
+    full = torch.from_numpy(case.rf).cuda()
+    host = torch.from_numpy(case.rf).pin_memory()
+    part = torch.empty_like(full)
+    if full.dtype == torch.int16:
+        part.fill_(32767)
+    else:
+        part.fill_(float("nan"))
+    boxes = _boxes(case, 4)
+    wf.copy_rf_boxes(host, part, boxes)
+
+    def das(rf):
+        if case.mode == "stai":
+            return wf.das_stai(rf, pr, gr, tx_elem=case.tx_elem, t_start=case.t_start,
+                               rf_scale=case.rf_scale)
+        return wf.das_pwi(rf, pr, gr, angles=case.angles, t_start=case.t_starts,
+                          rf_scale=case.rf_scale)
+
+    want, got = das(full), das(part)
+    torch.cuda.synchronize()
+    assert torch.isfinite(got).all()
+    assert torch.equal(got, want)
+    # device-to-device copies take the same path
+    part2 = torch.zeros_like(full)
+    wf.copy_rf_boxes(full, part2, boxes)
+    assert torch.equal(das(part2), want)
