@@ -176,3 +176,20 @@ def test_das_from_boxes_is_bit_identical(name, dtype):
     part2 = torch.zeros_like(full)
     wf.copy_rf_boxes(full, part2, boxes)
     assert torch.equal(das(part2), want)
+
+
+def test_copy_rejects_boxes_outside_the_array():
+    """Argument checks run on the host before any copy is queued (no device needed)."""
+    import ctypes as C
+    lib = wf._load()
+    src, dst = C.c_void_p(1 << 20), C.c_void_p(2 << 20)   # never dereferenced: every call fails its checks
+
+    def call(box, n_tx=4, n_rx=8, ns=64, eb=2):
+        arr = (wf._WfRfBox * 1)(wf._WfRfBox(*box))
+        return lib.wf_copy_rf_boxes(src, dst, n_tx, n_rx, ns, eb, arr, 1, None)
+
+    for bad in [(0, 5, 0, 8, 0, 64), (2, 2, 0, 8, 0, 64), (0, 4, -1, 8, 0, 64), (0, 4, 0, 9, 0, 64),
+                (0, 4, 0, 8, 8, 8), (0, 4, 0, 8, 0, 65), (-1, 4, 0, 8, 0, 64)]:
+        assert call(bad) == 1, bad
+    assert call((0, 4, 0, 8, 0, 64), eb=3) == 1
+    assert lib.wf_copy_rf_boxes(None, dst, 4, 8, 64, 2, None, 0, None) == 1
