@@ -512,11 +512,24 @@ void staged_hulls(int mode, const wf_probe* p, const wf_grid* g, const DasArgs& 
             return;
         }
     }
+    // A tiling whose tiles split another's (same columns, rows a divisor) stages
+    // subsets of the other's windows: its tiles are sub-rectangles with element
+    // ranges no wider, so only the coarsest of such tilings is scanned.
+    auto cols_of = [](const Cfg& c) { return 8 * c.wcol; };
+    auto rows_of = [](const Cfg& c) { return (32 / c.wcol) * c.p; };
+    std::sort(tiled.begin(), tiled.end(), [&](const Cfg& x, const Cfg& y) { return rows_of(x) > rows_of(y); });
+    std::vector<Cfg> scan;
+    for (const Cfg& c : tiled) {
+        bool covered = false;
+        for (const Cfg& o : scan)
+            covered = covered || (cols_of(o) == cols_of(c) && rows_of(o) % rows_of(c) == 0);
+        if (!covered) scan.push_back(c);
+    }
     const double two_f = 2.0 * (p->apod == WF_APOD_NONE ? 1.0 : p->f_number);
     constexpr int kMate = kC - 1;
     std::vector<double> bmn, bmx, rmn, rmx;
-    for (const Cfg& cfg : tiled) {
-        const int cols = 8 * cfg.wcol, rows = (32 / cfg.wcol) * cfg.p;
+    for (const Cfg& cfg : scan) {
+        const int cols = cols_of(cfg), rows = rows_of(cfg);
         const int tiles_x = (g->nx + cols - 1) / cols, tiles_z = (g->nz + rows - 1) / rows;
         for (int tz = 0; tz < tiles_z; ++tz)
             for (int tx = 0; tx < tiles_x; ++tx) {
