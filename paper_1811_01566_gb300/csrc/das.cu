@@ -492,9 +492,8 @@ void staged_hulls(int mode, const wf_probe* p, const wf_grid* g, const DasArgs& 
     Geom G;
     GeomD D;
     make_geom(p, g, G, D);
-    const bool sym_possible = mode == 0 && n_tx == E &&
-                              [&] { for (int t = 0; t < n_tx; ++t) if ((tx_elem ? tx_elem[t] : t) != t) return false;
-                                    return true; }();
+    bool sym_possible = mode == 0 && n_tx == E;   // reciprocal pairing: every element fires, in order
+    for (int t = 0; sym_possible && t < n_tx; ++t) sym_possible = (tx_elem ? tx_elem[t] : t) == t;
     const Cfg* cfgs = mode == 0 ? kStaiCfgs : kPwiCfgs;
     std::vector<Cfg> tiled;
     for (int sym = 0; sym <= (sym_possible ? 1 : 0); ++sym) {
