@@ -193,3 +193,79 @@ def test_copy_rejects_boxes_outside_the_array():
         assert call(bad) == 1, bad
     assert call((0, 4, 0, 8, 0, 64), eb=3) == 1
     assert lib.wf_copy_rf_boxes(None, dst, 4, 8, 64, 2, None, 0, None) == 1
+
+
+def _kernel_windows(case, ns):
+    """The staging windows of the tiled DAS kernels, restated in float32 from their rules
+    (tile element range, convex delay bounds of each (transmit, receive chunk) stage over the
+    tile rectangle, window start / length rounding), for both tile shapes and, where every
+    element fires in order, both pairings.  Yields (transmit, receive, first, end) per trace read."""
+    f32 = np.float32
+    E = case.n_elements
+    sc = case.fs / case.c
+    gx0, gz0 = f32(case.x_min * sc), f32(case.z_min * sc)
+    gdx = f32((case.x_max - case.x_min) / (case.nx - 1) * sc) if case.nx > 1 else f32(0)
+    gdz = f32((case.z_max - case.z_min) / (case.nz - 1) * sc) if case.nz > 1 else f32(0)
+    xe0, pitch = f32(-0.5 * (E - 1) * case.pitch * sc), f32(case.pitch * sc)
+    two_f = f32(2.0 * (1.0 if case.apod == wf.NONE else case.f_number))
+    xe = (xe0 + np.arange(E, dtype=f32) * pitch).astype(f32)
+    stai = case.mode == "stai"
+    tx_e = case.tx_elem if stai else None
+    t0 = [f32(case.t_start * case.fs)] * case.n_tx if stai else [f32(v * case.fs) for v in case.t_starts]
+    syms = [False, True] if stai and case.n_tx == E and all(int(e) == i for i, e in enumerate(tx_e)) else [False]
+    for rows in (32, 16):
+        for tz in range((case.nz + rows - 1) // rows):
+            for tx in range((case.nx + 31) // 32):
+                xlo, xhi = f32(gx0 + f32(tx * 32) * gdx), f32(gx0 + f32(tx * 32 + 31) * gdx)
+                zlo, zhi = f32(gz0 + f32(tz * rows) * gdz), f32(gz0 + f32(tz * rows + rows - 1) * gdz)
+                if case.apod == wf.NONE:
+                    elo, ehi = 0, E - 1
+                else:
+                    if not zhi > 0:
+                        continue
+                    half = f32(zhi / two_f)
+                    elo = max(int(np.floor(f32(f32(xlo - half - xe0) / pitch))) - 1, 0)
+                    ehi = min(int(np.ceil(f32(f32(xhi + half - xe0) / pitch))) + 1, E - 1)
+                    if elo > ehi:
+                        continue
+                for sym in syms:
+                    for k in range((ehi - elo + 1 + 7) // 8):
+                        r0, rl = elo + 8 * k, min(elo + 8 * k + 7, ehi)
+                        tlist = range(elo, rl + 1) if sym else \
+                            [t for t in range(case.n_tx) if not stai or elo <= tx_e[t] <= ehi]
+                        for t in tlist:
+                            rr = np.arange(max(r0, t) if sym else r0, rl + 1)
+                            xr = xe[rr]
+                            if stai:
+                                xt = xe[tx_e[t] if not sym else t]
+                                xm = np.clip(f32(0.5) * (xt + xr), xlo, xhi).astype(f32)
+                                mn = np.sqrt((xm - xt) ** 2 + zlo * zlo) + np.sqrt((xm - xr) ** 2 + zlo * zlo)
+                                mx = np.maximum(np.sqrt((xlo - xt) ** 2 + zhi * zhi) + np.sqrt((xlo - xr) ** 2 + zhi * zhi),
+                                                np.sqrt((xhi - xt) ** 2 + zhi * zhi) + np.sqrt((xhi - xr) ** 2 + zhi * zhi))
+                            else:
+                                sn, cs = f32(np.sin(case.angles[t])), f32(np.cos(case.angles[t]))
+                                xm = np.clip(xr - zlo * (sn / cs), xlo, xhi).astype(f32)
+                                mn = xm * sn + zlo * cs + np.sqrt((xm - xr) ** 2 + zlo * zlo)
+                                mx = np.maximum(xlo * sn + zhi * cs + np.sqrt((xlo - xr) ** 2 + zhi * zhi),
+                                                xhi * sn + zhi * cs + np.sqrt((xhi - xr) ** 2 + zhi * zhi))
+                            lo = (int(np.floor(f32(mn.min() - t0[t]))) - 2) & ~7
+                            ln = ((int(np.ceil(f32(mx.max() - t0[t]))) + 2 - lo + 1) + 7) & ~7
+                            if lo + ln <= 0 or lo > ns - 2:
+                                continue
+                            a, b = max(lo, 0), min(lo + ln + 8, ns)
+                            for r in rr:
+                                yield t, int(r), a, b
+                                if sym and r > t:
+                                    yield int(r), t, a, b
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_boxes_hold_every_staged_window(name):
+    """Every window the kernels stage (restated from their rules) lies inside the plan."""
+    case = configs.random_case(**CASES[name])
+    cov = _covered(case, _boxes(case, 4))
+    n = 0
+    for t, r, a, b in _kernel_windows(case, case.n_samples):
+        assert cov[t, r, a:b].all(), (name, t, r, a, b)
+        n += 1
+    assert n > 0
