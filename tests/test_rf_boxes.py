@@ -7,6 +7,9 @@ element firing (reciprocal pairing), STAI on a transmit subset, PWI, a
 non-zero t_start and every apodization; boxes stay inside the array; coarse
 grids that go to the per-pixel path get whole traces.  The delays here are
 the paper's formulas in float64, independent of the planner's tile bounds.
+A second CPU check restates the kernels' own staging rules in float32 (tile
+element ranges, per-stage convex bounds, window rounding) and requires every
+staged window inside the plan.
 
 GPU: DAS on a device buffer that received only the boxes (everything else
 poisoned: NaN for float RF, which any staged-but-missing sample would carry
