@@ -6,7 +6,8 @@ envelope (analytic signal + magnitude) and log-clip, for the full STAI
 workload (128 transmits x 128 receives x 2048 int16 samples, 512 x 256 grid,
 Hann apodization F = 1.5) on synthetic speckle/cyst/wire RF.  RF and outputs
 are resident in HBM for ``value``; ``e2e`` copies every frame's RF in from
-pinned host memory and the dB image back out inside the timed region.
+pinned host memory (the boxes of the transfer plan: the samples the DAS call
+can read) and the dB image back out inside the timed region.
 
 Several GPUs (torchrun) run independent replicas: the path has no exchange
 step, so there is no collective on the data path; the job throughput is the
