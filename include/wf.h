@@ -370,8 +370,13 @@ wf_status wf_fir_bandpass(double f_lo, double f_hi, double fs, int32_t n_taps, f
  *    contents: calls that overlap on the GPU (different streams, or host
  *    threads without ordering between them) race and may return wrong images.
  *    Order such calls on one stream.
+ *  - Kernel status flags (a bounded copy wait that ran out, an over-long
+ *    staging window) land in the array's status block, which the caller cannot
+ *    address: read them with wf_fixed_scratch_check.
  * Arguments, layouts and the rest of the error behaviour are those of
- * wf_das_stai.
+ * wf_das_stai, with one ordering difference: the checks that need no pointer
+ * (sizes, counts, values) come first and return WF_ERR_INVALID_ARG as there,
+ * then the size refusal (WF_ERR_WORKSPACE), then the pointer checks.
  */
 #define WF_FIXED_SCRATCH_BYTES (32u << 20)
 wf_status wf_das_stai_fixed_scratch(const wf_probe* probe, const wf_grid* grid, int32_t batch,
@@ -381,6 +386,30 @@ wf_status wf_das_stai_fixed_scratch(const wf_probe* probe, const wf_grid* grid, 
 
 /* Size in bytes of the fixed scratch array behind wf_das_stai_fixed_scratch. */
 size_t wf_fixed_scratch_bytes(void);
+
+/*
+ * The wf_workspace_check of the fixed scratch array (no counterpart in the
+ * paper): synchronises `stream`, reports WF_ERR_INTERNAL if a kernel of
+ * wf_das_stai_fixed_scratch recorded an internal inconsistency in the array's
+ * status block since that call began, WF_OK otherwise, and then clears the
+ * status block (a blocking memset on the current device).  Blocks the host.
+ */
+wf_status wf_fixed_scratch_check(wf_stream stream);
+
+/*
+ * Plans and tuning.  wf_das_stai / wf_das_pwi plan a call (tile configuration,
+ * staging, workspace layout, the CTA schedule over the pixel tiles) from its
+ * probe, grid, scan, batch and RF shape and type, and keep the plan with the
+ * packed kernel arguments in a small host-side cache (64 most recently used
+ * keys), so a repeated call with the same geometry only sets its pointers and
+ * launches.  Element weights are device data, read at run time, and not part
+ * of a plan.  The optional tuning switches (environment variables
+ * WF_DAS_NO_SYM, WF_DAS_NO_TMA, WF_DAS_TILE, WF_DAS_GROUPS, WF_DAS_BUDGET,
+ * WF_DAS_RING, WF_CHECK_BOUNDS) are read on the first DAS call;
+ * wf_das_reload_tuning re-reads them and drops every cached plan.  Host only;
+ * safe to call from any thread between calls.
+ */
+wf_status wf_das_reload_tuning(void);
 
 /*
  * Synchronises `stream` and reports whether a DAS kernel that used `ws`

@@ -25,7 +25,7 @@ __all__ = ["Probe", "Grid", "WfError", "HANN", "RECT", "NONE", "das_stai", "das_
            "das_workspace_bytes", "das_delays", "das_backward", "das", "envelope", "logclip",
            "envelope_backward", "logclip_backward", "bmode", "bmode_diff", "fir", "iq_demod",
            "fir_bandpass", "workspace_check", "rf_boxes", "copy_rf_boxes", "library_path",
-           "version"]
+           "version", "reload_tuning"]
 
 HANN, RECT, NONE = 0, 1, 2
 _DTYPES = {torch.float32: 0, torch.float16: 1, torch.int16: 2}
@@ -108,6 +108,8 @@ def _load():
             lib.wf_das_rf_boxes.restype = C.c_int
             lib.wf_copy_rf_boxes.argtypes = [vp, vp, i32, i32, i32, i32, vp, i32, vp]
             lib.wf_copy_rf_boxes.restype = C.c_int
+            lib.wf_das_reload_tuning.argtypes = []
+            lib.wf_das_reload_tuning.restype = C.c_int
             lib.wf_workspace_check.argtypes = [vp, sz, vp]
             lib.wf_workspace_check.restype = C.c_int
             lib.wf_status_string.argtypes = [C.c_int]
@@ -191,10 +193,24 @@ def _prep(rf, probe, grid, out, workspace):
     b, n_tx, n_rx, ns = rf.shape
     if out is None:
         out = torch.empty(b, grid.nz, grid.nx, device=rf.device, dtype=torch.float32)
-    need = das_workspace_bytes(probe, grid, b, n_tx)
-    if workspace is None:
-        workspace = torch.empty(need, device=rf.device, dtype=torch.uint8)
+    if workspace is None:   # a caller's workspace is size-checked by the library itself
+        workspace = torch.empty(das_workspace_bytes(probe, grid, b, n_tx), device=rf.device,
+                                dtype=torch.uint8)
     return rf, out, workspace
+
+
+def _f64_array(values, n: int):
+    """ctypes double[n] of a sequence (numpy float64 arrays are passed without a copy loop)."""
+    import numpy as np
+    a = np.ascontiguousarray(values, dtype=np.float64)
+    if a.size != n:
+        raise ValueError(f"expected {n} values, got {a.size}")
+    return (C.c_double * n).from_buffer_copy(a.data)
+
+
+def reload_tuning() -> None:
+    """Re-read the WF_DAS_* / WF_CHECK_BOUNDS tuning switches and drop cached plans."""
+    _check(_load().wf_das_reload_tuning(), "wf_das_reload_tuning")
 
 
 def das_stai(rf: torch.Tensor, probe: Probe, grid: Grid, *, tx_elem=None, t_start: float = 0.0,
@@ -220,8 +236,8 @@ def das_pwi(rf: torch.Tensor, probe: Probe, grid: Grid, *, angles, t_start=None,
     """PWI delay-and-sum with coherent compounding -> [batch, nz, nx] (float32); see wf_das_pwi."""
     rf, out, ws = _prep(rf, probe, grid, out, workspace)
     b, n_ang, n_rx, ns = rf.shape
-    ang = (C.c_double * n_ang)(*[float(v) for v in angles])
-    ts = None if t_start is None else (C.c_double * n_ang)(*[float(v) for v in t_start])
+    ang = _f64_array(angles, n_ang)
+    ts = None if t_start is None else _f64_array(t_start, n_ang)
     st = _load().wf_das_pwi(C.byref(probe._c()), C.byref(grid._c()), b, n_ang, ang, ts, n_rx, ns,
                             _DTYPES[rf.dtype], rf.data_ptr(), float(rf_scale), out.data_ptr(),
                             ws.data_ptr(), ws.numel() * ws.element_size(), _stream(stream))

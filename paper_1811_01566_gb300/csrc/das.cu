@@ -5,11 +5,16 @@
 // das_check.cu (bounds-checked variants).
 #include <algorithm>
 #include <cmath>
-#include <numeric>
-#include <vector>
-#include <cstdlib>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <list>
+#include <memory>
+#include <mutex>
+#include <numeric>
+#include <string>
+#include <unordered_map>
+#include <vector>
 
 #include "das_kernels.cuh"
 
@@ -89,6 +94,49 @@ namespace {
 
 bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
 
+// Tuning switches from the environment (WF_DAS_NO_SYM, WF_DAS_NO_TMA, WF_DAS_TILE,
+// WF_DAS_GROUPS, WF_DAS_BUDGET, WF_DAS_RING, WF_CHECK_BOUNDS), read on the first DAS
+// call and again only on wf_das_reload_tuning(); `gen` counts the reloads, so plans
+// cached under older switches are never reused.
+struct Tuning {
+    bool no_sym = false, no_tma = false, check_bounds = false;
+    int tile_w = 0, tile_p = 0;   // 0: no tile override
+    int groups = 0;               // > 0: uniform groups instead of the schedule
+    int budget = 0;               // > 0: CTAs per frame of the schedule
+    int ring = 0;                 // > 0: TMA ring depth cap
+    unsigned gen = 0;
+};
+
+std::mutex g_tuning_mu;
+Tuning g_tuning;
+bool g_tuning_read = false;
+
+bool env_flag(const char* name) {
+    const char* v = std::getenv(name);
+    return v && v[0] && v[0] != '0';
+}
+
+void read_tuning_locked() {
+    Tuning t;
+    t.gen = g_tuning.gen + 1;
+    t.no_sym = env_flag("WF_DAS_NO_SYM");
+    t.no_tma = env_flag("WF_DAS_NO_TMA");
+    t.check_bounds = env_flag("WF_CHECK_BOUNDS");
+    if (const char* v = std::getenv("WF_DAS_TILE"))
+        if (std::sscanf(v, "%d,%d", &t.tile_w, &t.tile_p) != 2) t.tile_w = t.tile_p = 0;
+    if (const char* v = std::getenv("WF_DAS_GROUPS")) t.groups = std::max(0, std::atoi(v));
+    if (const char* v = std::getenv("WF_DAS_BUDGET")) t.budget = std::max(0, std::atoi(v));
+    if (const char* v = std::getenv("WF_DAS_RING")) t.ring = std::max(0, std::atoi(v));
+    g_tuning = t;
+    g_tuning_read = true;
+}
+
+Tuning tuning() {
+    std::lock_guard<std::mutex> lk(g_tuning_mu);
+    if (!g_tuning_read) read_tuning_locked();
+    return g_tuning;
+}
+
 wf_status check_probe_grid(const wf_probe* p, const wf_grid* g) {
     if (!p || !g) return WF_ERR_INVALID_ARG;
     if (p->n_elements < 1 || p->n_elements > WF_MAX_ELEMENTS) return WF_ERR_INVALID_ARG;
@@ -164,8 +212,7 @@ constexpr int kTargetItemsStai = 768;
 // weights.  WF_DAS_NO_SYM=1 turns it off (testing the general path).
 bool use_sym(int mode, int n_tx, int n_elements, const int32_t* tx_elem) {
     if (mode != 0 || n_tx != n_elements) return false;
-    const char* v = std::getenv("WF_DAS_NO_SYM");
-    if (v && v[0] && v[0] != '0') return false;
+    if (tuning().no_sym) return false;
     if (tx_elem)
         for (int t = 0; t < n_tx; ++t)
             if (tx_elem[t] != t) return false;
@@ -186,9 +233,9 @@ int window_bound(const GeomD& D, int cols, int rows) {
 // Optional tuning override "wcol,p" (WF_DAS_TILE); ignored unless it names a
 // configuration of this mode that fits.
 bool tile_override(int mode, Cfg& out) {
-    const char* v = std::getenv("WF_DAS_TILE");
-    int w = 0, p = 0;
-    if (!v || std::sscanf(v, "%d,%d", &w, &p) != 2) return false;
+    const Tuning tu = tuning();
+    const int w = tu.tile_w, p = tu.tile_p;
+    if (w == 0) return false;
     const Cfg* cfgs = mode == 0 ? kStaiCfgs : kPwiCfgs;
     for (int i = 0; i < 2; ++i)
         if (cfgs[i].wcol == w && cfgs[i].p == p) {
@@ -200,6 +247,7 @@ bool tile_override(int mode, Cfg& out) {
 
 Plan plan_for(int mode, const Cfg& cfg, const GeomD& D, const wf_probe* p, const wf_grid* g,
               int batch, int n_tx, int ns, int rf_bytes, bool sym) {
+    const Tuning tu = tuning();
     Plan P{};
     P.cfg = cfg;
     P.cols = 8 * cfg.wcol;
@@ -210,28 +258,26 @@ Plan plan_for(int mode, const Cfg& cfg, const GeomD& D, const wf_probe* p, const
     P.tiles_z = (g->nz + P.rows - 1) / P.rows;
     const long long tiles = (long long)P.tiles_x * P.tiles_z * batch;
     P.n_groups = (int)std::min<long long>(kMaxGroups, std::max<long long>(1, (kTargetItems + tiles - 1) / tiles));
-    if (const char* v = std::getenv("WF_DAS_GROUPS"))   // tuning override
-        P.n_groups = std::max(1, std::min(kMaxGroups, std::atoi(v)));
+    if (tu.groups > 0) P.n_groups = std::min(kMaxGroups, tu.groups);   // tuning override
     P.n_items = P.tiles_x * P.tiles_z * P.n_groups;
     // Work-proportional schedule (built per call from the scan geometry): budget CTAs per
     // frame plus at most one extra per tile from rounding.
     // CTAs per frame: reciprocal STAI tiles carry more start-up per stage (window
     // bounds of pair sums, two traces per row), so they take fewer, longer CTAs.
     long long target_items = mode == 0 ? kTargetItemsStai : kTargetItems;
-    if (const char* v = std::getenv("WF_DAS_BUDGET")) target_items = std::max(1, std::atoi(v));   // tuning
+    if (tu.budget > 0) target_items = tu.budget;   // tuning
     P.budget = (int)std::max<long long>(1, (target_items + batch - 1) / batch);
-    P.table = (long long)P.budget + P.tiles_x * P.tiles_z <= kMaxItems && !std::getenv("WF_DAS_GROUPS");
+    P.table = (long long)P.budget + P.tiles_x * P.tiles_z <= kMaxItems && tu.groups == 0;
     P.info_bytes = (((size_t)P.tiles_x * P.tiles_z * sizeof(unsigned)) + 255) & ~(size_t)255;
     P.sym = sym && mode == 0;
     // TMA bulk copies need 16-byte aligned trace windows: samples per trace a multiple of 8.
     // WF_DAS_NO_TMA=1 selects the register-staged path instead (tuning and testing).
-    const char* no_tma = std::getenv("WF_DAS_NO_TMA");
-    P.tma = ns % 8 == 0 && !(no_tma && no_tma[0] && no_tma[0] != '0');
+    P.tma = ns % 8 == 0 && !tu.no_tma;
     // Deepest TMA ring (stages in flight) that fits two CTAs per SM, double-buffered pairs
     // preferred; WF_DAS_RING=n caps the depth (tuning).
     bool found = false;
     int max_ring = kMaxRing;
-    if (const char* r = std::getenv("WF_DAS_RING")) max_ring = std::max(2, std::min(kMaxRing, std::atoi(r)));
+    if (tu.ring > 0) max_ring = std::max(2, std::min(kMaxRing, tu.ring));
     struct Cand { bool db; int ring; };
     Cand cands[2 * kMaxRing + 2];
     int nc = 0;
@@ -283,10 +329,7 @@ Plan make_plan(int mode, const wf_probe* p, const wf_grid* g, int batch, int n_t
     return P;
 }
 
-bool check_bounds_mode() {
-    const char* v = std::getenv("WF_CHECK_BOUNDS");
-    return v && v[0] && v[0] != '0';
-}
+bool check_bounds_mode() { return tuning().check_bounds; }
 
 template <int MODE>
 wf_status dispatch(DasArgs& A, const Plan& P, int batch, wf_dtype dt, cudaStream_t st) {
@@ -379,10 +422,99 @@ int build_schedule(int mode, const wf_probe* p, const wf_grid* g, const Plan& P,
     return n;
 }
 
-wf_status das_common(int mode, const wf_probe* probe, const wf_grid* grid, int32_t batch,
-                     int32_t n_tx, int32_t n_rx, int32_t n_samples, wf_dtype dtype,
-                     const void* rf, float rf_scale, float* out, void* ws, size_t ws_bytes,
-                     wf_stream stream, DasArgs& A, double tx_extra, bool sym) {
+double fill_tx(DasArgs& a, const wf_probe* probe, int mode, int n_tx, const int32_t* tx_elem,
+               const double* angles, const double* t_start, bool per_tx_start);
+
+// ---------------------------------------------------------------------------
+// Plan cache.  A DAS call's plan (tile configuration, staging, workspace layout),
+// its transmit table and its CTA schedule depend only on the probe, grid, scan,
+// batch, RF shape and type and the tuning switches, so they are built once per
+// such key and kept, with the packed kernel arguments, in a small LRU cache: a
+// repeated call copies the cached argument block, sets its pointers and
+// launches.  Element weights are device data and not part of the key.
+// ---------------------------------------------------------------------------
+struct CachedPlan {
+    Plan P;
+    std::unique_ptr<DasArgs> A;   // everything but the per-call pointers and rf_scale
+};
+
+class PlanCache {
+  public:
+    std::shared_ptr<const CachedPlan> get(const std::string& key) {
+        std::lock_guard<std::mutex> lk(mu_);
+        auto it = map_.find(key);
+        if (it == map_.end()) return nullptr;
+        lru_.splice(lru_.begin(), lru_, it->second.first);
+        return it->second.second;
+    }
+    void put(const std::string& key, std::shared_ptr<const CachedPlan> v) {
+        std::lock_guard<std::mutex> lk(mu_);
+        auto it = map_.find(key);
+        if (it != map_.end()) {
+            lru_.erase(it->second.first);
+            map_.erase(it);
+        }
+        lru_.push_front(key);
+        map_.emplace(key, std::make_pair(lru_.begin(), std::move(v)));
+        while (map_.size() > kCapacity) {
+            map_.erase(lru_.back());
+            lru_.pop_back();
+        }
+    }
+    void clear() {
+        std::lock_guard<std::mutex> lk(mu_);
+        map_.clear();
+        lru_.clear();
+    }
+
+  private:
+    static constexpr size_t kCapacity = 64;
+    std::mutex mu_;
+    std::list<std::string> lru_;   // most recent first
+    std::unordered_map<std::string,
+                       std::pair<std::list<std::string>::iterator, std::shared_ptr<const CachedPlan>>>
+        map_;
+};
+
+PlanCache g_plans;
+
+struct KeyBuf {
+    std::string s;
+    template <typename T>
+    void add(const T& v) { s.append(reinterpret_cast<const char*>(&v), sizeof(T)); }
+    void add_bytes(const void* p, size_t n) { s.append(static_cast<const char*>(p), n); }
+};
+
+// Everything a plan depends on, field by field (no struct padding in the key).
+std::string plan_key(int mode, const wf_probe* p, const wf_grid* g, int batch, int n_tx,
+                     const int32_t* tx_elem, const double* angles, const double* t_start, int ns,
+                     wf_dtype dtype, unsigned gen) {
+    KeyBuf k;
+    k.s.reserve(128 + (size_t)n_tx * 16);
+    k.add(mode); k.add(gen); k.add(batch); k.add(n_tx); k.add(ns); k.add((int)dtype);
+    k.add(p->n_elements); k.add(p->pitch); k.add(p->fs); k.add(p->c); k.add(p->f_number);
+    k.add(p->apod);
+    k.add(g->nz); k.add(g->nx); k.add(g->x_min); k.add(g->x_max); k.add(g->z_min); k.add(g->z_max);
+    if (mode == 0) {
+        k.add((int)(tx_elem != nullptr));
+        if (tx_elem) k.add_bytes(tx_elem, (size_t)n_tx * sizeof(int32_t));
+        k.add(t_start[0]);
+    } else {
+        k.add_bytes(angles, (size_t)n_tx * sizeof(double));
+        k.add((int)(t_start != nullptr));
+        if (t_start) k.add_bytes(t_start, (size_t)n_tx * sizeof(double));
+    }
+    return k.s;
+}
+
+// The delay-and-sum call of both transmit schemes: host checks, cached plan, launch.
+// STAI passes tx_elem and t_start[0]; PWI passes angles and t_start[n_tx] (or NULL).
+wf_status das_run(int mode, const wf_probe* probe, const wf_grid* grid, int32_t batch,
+                  int32_t n_tx, const int32_t* tx_elem, const double* angles,
+                  const double* t_start, int32_t n_rx, int32_t n_samples, wf_dtype dtype,
+                  const void* rf, float rf_scale, float* out, void* ws, size_t ws_bytes,
+                  wf_stream stream) {
+    thread_local DasArgs A;  // ~18 KB parameter block, copied into the launch
     wf_status s = check_probe_grid(probe, grid);
     if (s != WF_OK) return s;
     if (batch < 1 || batch > 65535) return WF_ERR_INVALID_ARG;
@@ -393,32 +525,52 @@ wf_status das_common(int mode, const wf_probe* probe, const wf_grid* grid, int32
     if (dtype == WF_I16 && !std::isfinite(rf_scale)) return WF_ERR_INVALID_ARG;
     if (!rf || !out) return WF_ERR_INVALID_ARG;
     if (((uintptr_t)rf & 15u) || ((uintptr_t)out & 3u)) return WF_ERR_INVALID_ARG;
-    if (2.0 * max_delay(probe, grid) + tx_extra >= 4194304.0) return WF_ERR_UNSUPPORTED;
-    const Plan P = make_plan(mode, probe, grid, batch, n_tx, n_samples, dtype == WF_F32 ? 4 : 2, sym);
+    const Tuning tu = tuning();
+    const std::string key =
+        plan_key(mode, probe, grid, batch, n_tx, tx_elem, angles, t_start, n_samples, dtype, tu.gen);
+    std::shared_ptr<const CachedPlan> e = g_plans.get(key);
+    if (!e) {
+        auto ne = std::make_shared<CachedPlan>();
+        ne->A = std::make_unique<DasArgs>();
+        DasArgs& T = *ne->A;
+        std::memset(&T, 0, sizeof(T));
+        const double extra = fill_tx(T, probe, mode, n_tx, tx_elem, angles, t_start, mode == 1);
+        if (extra < 0.0) return WF_ERR_INVALID_ARG;
+        if (2.0 * max_delay(probe, grid) + extra >= 4194304.0) return WF_ERR_UNSUPPORTED;
+        const bool sym = use_sym(mode, n_tx, probe->n_elements, tx_elem);
+        const Plan P = make_plan(mode, probe, grid, batch, n_tx, n_samples, dtype == WF_F32 ? 4 : 2, sym);
+        ne->P = P;
+        make_geom(probe, grid, T.g, T.gd);
+        T.g.elem_weight = nullptr;
+        T.n_tx = n_tx;
+        T.ns = n_samples;
+        T.tiles_x = P.tiles_x;
+        T.tiles_z = P.tiles_z;
+        T.n_groups = P.n_groups;
+        T.n_items = P.n_items;
+        T.sym = P.sym ? 1 : 0;
+        T.W = P.W;
+        T.ring = P.ring;
+        T.frame_elems = (long long)n_tx * probe->n_elements * n_samples;
+        T.use_table = 0;
+        if (P.tiled && P.table) {
+            T.use_table = 1;
+            T.n_items = build_schedule(mode, probe, grid, P, T);
+        }
+        g_plans.put(key, ne);
+        e = ne;
+    }
+    const Plan& P = e->P;
     if (!ws || ((uintptr_t)ws & 15u)) return WF_ERR_WORKSPACE;
     if (ws_bytes < P.ws_bytes) return WF_ERR_WORKSPACE;
-    make_geom(probe, grid, A.g, A.gd);
-    A.n_tx = n_tx;
-    A.ns = n_samples;
-    A.tiles_x = P.tiles_x;
-    A.tiles_z = P.tiles_z;
-    A.n_groups = P.n_groups;
-    A.n_items = P.n_items;
-    A.sym = P.sym ? 1 : 0;
-    A.W = P.W;
-    A.ring = P.ring;
+    A = *e->A;
+    A.g.elem_weight = probe->elem_weight;
     A.rf = rf;
     A.rf_scale = dtype == WF_I16 ? rf_scale : 1.0f;
-    A.frame_elems = (long long)n_tx * probe->n_elements * n_samples;
     A.hdr = static_cast<WsHeader*>(ws);
     A.tile_info = reinterpret_cast<unsigned*>(static_cast<char*>(ws) + kWsHeaderBytes);
     A.part = reinterpret_cast<float*>(static_cast<char*>(ws) + kWsHeaderBytes + P.info_bytes);
     A.out = out;
-    A.use_table = 0;
-    if (P.tiled && P.table) {
-        A.use_table = 1;
-        A.n_items = build_schedule(mode, probe, grid, P, A);
-    }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if ((s = cuda_status(cudaMemsetAsync(ws, 0, kWsHeaderBytes + P.info_bytes, st))) != WF_OK) return s;
     return mode == 0 ? dispatch<0>(A, P, batch, dtype, st) : dispatch<1>(A, P, batch, dtype, st);
@@ -689,15 +841,9 @@ extern "C" wf_status wf_das_stai(const wf_probe* probe, const wf_grid* grid, int
                                  int32_t n_samples, double t_start, wf_dtype dtype, const void* rf,
                                  float rf_scale, float* out, void* ws, size_t ws_bytes,
                                  wf_stream stream) {
-    thread_local DasArgs local;  // ~10 KB parameter block, copied into the launch
-    DasArgs& a = local;
     if (!probe || !std::isfinite(t_start)) return WF_ERR_INVALID_ARG;
-    if (n_tx < 1 || n_tx > WF_MAX_TX) return WF_ERR_INVALID_ARG;
-    if (check_probe_grid(probe, grid) != WF_OK) return WF_ERR_INVALID_ARG;
-    const double extra = fill_tx(a, probe, 0, n_tx, tx_elem, nullptr, &t_start, false);
-    if (extra < 0.0) return WF_ERR_INVALID_ARG;
-    return das_common(0, probe, grid, batch, n_tx, n_rx, n_samples, dtype, rf, rf_scale, out, ws,
-                      ws_bytes, stream, a, extra, use_sym(0, n_tx, probe->n_elements, tx_elem));
+    return das_run(0, probe, grid, batch, n_tx, tx_elem, nullptr, &t_start, n_rx, n_samples, dtype,
+                   rf, rf_scale, out, ws, ws_bytes, stream);
 }
 
 extern "C" wf_status wf_das_pwi(const wf_probe* probe, const wf_grid* grid, int32_t batch,
@@ -705,15 +851,18 @@ extern "C" wf_status wf_das_pwi(const wf_probe* probe, const wf_grid* grid, int3
                                 int32_t n_rx, int32_t n_samples, wf_dtype dtype, const void* rf,
                                 float rf_scale, float* out, void* ws, size_t ws_bytes,
                                 wf_stream stream) {
-    thread_local DasArgs local;
-    DasArgs& a = local;
     if (!probe || !angles_rad) return WF_ERR_INVALID_ARG;
-    if (n_angles < 1 || n_angles > WF_MAX_TX) return WF_ERR_INVALID_ARG;
-    if (check_probe_grid(probe, grid) != WF_OK) return WF_ERR_INVALID_ARG;
-    const double extra = fill_tx(a, probe, 1, n_angles, nullptr, angles_rad, t_start, true);
-    if (extra < 0.0) return WF_ERR_INVALID_ARG;
-    return das_common(1, probe, grid, batch, n_angles, n_rx, n_samples, dtype, rf, rf_scale, out,
-                      ws, ws_bytes, stream, a, extra, false);
+    return das_run(1, probe, grid, batch, n_angles, nullptr, angles_rad, t_start, n_rx, n_samples,
+                   dtype, rf, rf_scale, out, ws, ws_bytes, stream);
+}
+
+extern "C" wf_status wf_das_reload_tuning(void) {
+    {
+        std::lock_guard<std::mutex> lk(g_tuning_mu);
+        read_tuning_locked();
+    }
+    g_plans.clear();
+    return WF_OK;
 }
 
 extern "C" wf_status wf_das_delays(const wf_probe* probe, const wf_grid* grid, int32_t mode,
@@ -833,23 +982,21 @@ constexpr size_t kFixedScratchBytes = (size_t)WF_FIXED_SCRATCH_BYTES;
 static __device__ __align__(256) unsigned char g_fixed_scratch[kFixedScratchBytes];
 
 // Device address of g_fixed_scratch, looked up once per device with that device
-// current (in host code the symbol is only a host-side stand-in).
+// current (in host code the symbol is only a host-side stand-in).  The pointer is
+// published with an atomic store and read with an atomic load, so two host threads
+// making their first call on one device at once never race on it.
 constexpr int kMaxDevices = 64;
 void* g_scratch_ptr[kMaxDevices] = {};
-int g_scratch_ready[kMaxDevices] = {};
 
 wf_status fixed_scratch(void** out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return WF_ERR_CUDA;
     if (dev < 0 || dev >= kMaxDevices) return WF_ERR_UNSUPPORTED;
-    if (__atomic_load_n(&g_scratch_ready[dev], __ATOMIC_ACQUIRE)) {
-        *out = g_scratch_ptr[dev];
-        return WF_OK;
+    void* p = __atomic_load_n(&g_scratch_ptr[dev], __ATOMIC_ACQUIRE);
+    if (!p) {
+        if (cudaGetSymbolAddress(&p, g_fixed_scratch) != cudaSuccess || !p) return WF_ERR_CUDA;
+        __atomic_store_n(&g_scratch_ptr[dev], p, __ATOMIC_RELEASE);
     }
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_fixed_scratch) != cudaSuccess || !p) return WF_ERR_CUDA;
-    g_scratch_ptr[dev] = p;
-    __atomic_store_n(&g_scratch_ready[dev], 1, __ATOMIC_RELEASE);
     *out = p;
     return WF_OK;
 }
@@ -862,10 +1009,20 @@ extern "C" wf_status wf_das_stai_fixed_scratch(const wf_probe* probe, const wf_g
                                                int32_t n_rx, int32_t n_samples, double t_start,
                                                wf_dtype dtype, const void* rf, float rf_scale,
                                                float* out, wf_stream stream) {
-    if (check_probe_grid(probe, grid) != WF_OK || batch < 1 || n_tx < 1 || n_tx > WF_MAX_TX)
+    // The checks of wf_das_stai that need no pointer come first, so a bad size, count
+    // or value returns WF_ERR_INVALID_ARG exactly as there; the size refusal follows
+    // and precedes the pointer checks (an oversized call never looks at rf or out).
+    if (!probe || !std::isfinite(t_start)) return WF_ERR_INVALID_ARG;
+    if (check_probe_grid(probe, grid) != WF_OK || batch < 1 || batch > 65535 || n_tx < 1 ||
+        n_tx > WF_MAX_TX)
+        return WF_ERR_INVALID_ARG;
+    if (n_rx != probe->n_elements || n_samples < 1 || n_samples > WF_MAX_SAMPLES)
         return WF_ERR_INVALID_ARG;
     if (dtype != WF_F32 && dtype != WF_F16 && dtype != WF_I16) return WF_ERR_INVALID_ARG;
-    if (n_samples < 1 || n_samples > WF_MAX_SAMPLES) return WF_ERR_INVALID_ARG;
+    if (dtype == WF_I16 && !std::isfinite(rf_scale)) return WF_ERR_INVALID_ARG;
+    if (tx_elem)
+        for (int t = 0; t < n_tx; ++t)
+            if (tx_elem[t] < 0 || tx_elem[t] >= probe->n_elements) return WF_ERR_INVALID_ARG;
     const Plan P = make_plan(0, probe, grid, batch, n_tx, n_samples, dtype == WF_F32 ? 4 : 2,
                              use_sym(0, n_tx, probe->n_elements, tx_elem));
     if (P.ws_bytes > kFixedScratchBytes) return WF_ERR_WORKSPACE;
@@ -877,3 +1034,14 @@ extern "C" wf_status wf_das_stai_fixed_scratch(const wf_probe* probe, const wf_g
 }
 
 extern "C" size_t wf_fixed_scratch_bytes(void) { return kFixedScratchBytes; }
+
+extern "C" wf_status wf_fixed_scratch_check(wf_stream stream) {
+    void* ws = nullptr;
+    const wf_status s = fixed_scratch(&ws);
+    if (s != WF_OK) return s;
+    const wf_status r = wf_workspace_check(ws, kFixedScratchBytes, stream);
+    if (r == WF_ERR_CUDA) return r;
+    // clear the status block so the next check reports only what follows it
+    if (cudaMemset(ws, 0, kWsHeaderBytes) != cudaSuccess) return WF_ERR_CUDA;
+    return r;
+}

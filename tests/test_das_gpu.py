@@ -88,6 +88,7 @@ def test_staging_variants_agree_with_oracle(mode, monkeypatch):
             monkeypatch.delenv(k, raising=False)
         for k, v in env.items():
             monkeypatch.setenv(k, v)
+        wf.reload_tuning()
         got = das_gpu(case).cpu().numpy()[0]
         assert rel_l2(got, want) <= TOL_BF_REL_L2, env
         outs.append(got)
@@ -131,6 +132,7 @@ def test_deterministic_and_bounds_check_mode(monkeypatch):
     b = das_gpu(case, rf, ws).clone()
     assert torch.equal(a, b)
     monkeypatch.setenv("WF_CHECK_BOUNDS", "1")
+    wf.reload_tuning()
     c = das_gpu(case, rf, ws).clone()
     wf.workspace_check(ws)      # no staging window overflow, no gather outside its window
     assert torch.equal(a, c)

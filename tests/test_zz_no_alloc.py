@@ -29,6 +29,8 @@ def _lib():
     f.restype = C.c_int
     lib.wf_fixed_scratch_bytes.argtypes = []
     lib.wf_fixed_scratch_bytes.restype = C.c_size_t
+    lib.wf_fixed_scratch_check.argtypes = [C.c_void_p]
+    lib.wf_fixed_scratch_check.restype = C.c_int
     return lib
 
 
@@ -45,11 +47,21 @@ def test_fixed_scratch_size_is_exported_and_oversized_requests_are_refused():
     case = configs.random_case("stai", 1, n_elements=128, n_tx=128, n_samples=2048, nz=512, nx=256)
     pr, gr = _probe_grid(case)
     batch = 128
+    # every tiled plan needs more than the array at this batch: its workspace holds at least
+    # one float partial tile for every pixel tile of every frame, a whole image per frame
+    assert batch * case.nz * case.nx * 4 > cap
     assert wf.das_workspace_bytes(pr, gr, batch, 128) > cap
-    # refused on the host, before any device call: dummy (aligned) pointers are never touched
+    # Refused on the host before any device call.  rf and out are NULL: the size refusal
+    # precedes the pointer checks, so the status is WF_ERR_WORKSPACE; were the size check
+    # ever to let the call through, the NULL pointers would stop it with
+    # WF_ERR_INVALID_ARG before anything is launched.
     st = lib.wf_das_stai_fixed_scratch(C.byref(pr._c()), C.byref(gr._c()), batch, 128, None, 128,
-                                       2048, 0.0, 0, C.c_void_p(256), 1.0, C.c_void_p(256), None)
+                                       2048, 0.0, 0, None, 1.0, None, None)
     assert st == 4   # WF_ERR_WORKSPACE
+    # checks that need no pointer come first, as in wf_das_stai
+    st = lib.wf_das_stai_fixed_scratch(C.byref(pr._c()), C.byref(gr._c()), batch, 128, None, 127,
+                                       2048, 0.0, 0, None, 1.0, None, None)
+    assert st == 1   # WF_ERR_INVALID_ARG: n_rx differs from the element count
 
 
 @pytest.mark.gpu
@@ -77,6 +89,9 @@ def test_fixed_scratch_matches_workspace_entry_point(which):
                                            float(case.rf_scale), out.data_ptr(),
                                            C.c_void_p(stream.cuda_stream))
         assert st == 0, wf.WfError(st, "wf_das_stai_fixed_scratch")
+        # no kernel flagged the array's status block (bounded waits, window bounds)
+        chk = lib.wf_fixed_scratch_check(C.c_void_p(stream.cuda_stream))
+        assert chk == 0, wf.WfError(chk, "wf_fixed_scratch_check")
         torch.cuda.synchronize()
         got = out.cpu().numpy()
         assert np.isfinite(got).all()
