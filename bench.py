@@ -2,19 +2,23 @@
 """B-mode reconstruction throughput on GB300: frames/s of the full Fig. 2 pipeline.
 
 One step = one frame through the whole hot path: delay-and-sum (Sec. II-B),
-envelope (analytic signal + magnitude) and log-clip, for the full STAI
-workload (128 transmits x 128 receives x 2048 int16 samples, 512 x 256 grid,
-Hann apodization F = 1.5) on synthetic speckle/cyst/wire RF.  RF and outputs
-are resident in HBM for ``value``; ``e2e`` copies every frame's RF in from
-pinned host memory (the boxes of the transfer plan: the samples the DAS call
-can read) and the dB image back out inside the timed region.
+envelope (analytic signal + magnitude) and log-clip.  The default workload is
+the largest single-GPU one, plane-wave imaging with coherent compounding: 64
+steering angles (-16..16 deg) x 128 receives x 4096 int16 samples onto a 1024
+x 512 grid (5-45 mm), Hann apodization F = 1.5, on synthetic
+speckle/cyst/wire RF.  The same line carries the full STAI workload (128
+transmits x 128 receives x 2048 int16 samples, 512 x 256 grid) and the FP16
+storage variant of the PWI workload under ``extra``.  RF and outputs are
+resident in HBM for ``value``; ``e2e`` copies every frame's RF in from pinned
+host memory (the boxes of the transfer plan: the samples the DAS call can
+read) and the dB image back out inside the timed region.
 
 Several GPUs (torchrun) run independent replicas: the path has no exchange
 step, so there is no collective on the data path; the job throughput is the
 frames of all ranks over the slowest rank's time.
 
-``--impl reference`` times the FP64 CPU oracle on a bounded sample of the
-same workload (the deliberately slow baseline).
+``--impl reference`` times the FP64 CPU oracle on the same workload: full
+frames with the image rows split over every host core.
 """
 from __future__ import annotations
 
@@ -34,6 +38,10 @@ import torch  # noqa: E402
 
 L2_BYTES = 129 * 1024 * 1024
 FP32_OPS_PER_DELAY_SUM = 6   # delay add, floor, fraction, 2 interpolation, 1 accumulate FMA
+SMEM_WORDS_PER_CLOCK = 32    # shared-memory words (4 B) an SM delivers per clock
+WORDS_PER_DELAY_SUM = 2      # one staged FP32 pair (x[i], x[i+1] - x[i]) per delay-sum
+DEFAULT_WORKLOAD = "pwi_full_i16"
+EXTRA_WORKLOADS = ("stai_full", "pwi_full_f16")
 
 
 def parse():
@@ -42,7 +50,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
-    ap.add_argument("--workload", default="stai_full",
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
                     choices=["stai_full", "stai_small", "pwi_full_i16", "pwi_full_f16", "pwi_batch",
                              "served", "diff_pwi"])
     ap.add_argument("--rate", type=float, default=200.0, help="served: Poisson arrival rate (req/s)")
@@ -50,6 +58,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="CPU time budget of the oracle sample (cpu_baseline / reference arm)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="time only --workload (no extra workloads on the line)")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--profile-only", action="store_true",
                     help="only W + K eager pipeline steps (a short, clean command for ncu)")
@@ -190,7 +200,8 @@ class ClockSampler:
         use = inside or rows
         reasons = sorted({n for r in use for n, f in zip(self.NAMES, r[3]) if f.lower() == "active"})
         return {"sm_mhz": statistics.median(r[1] for r in use), "sm_max_mhz": max(r[2] for r in use),
-                "samples": len(use), "in_timed_region": bool(inside), "reasons": reasons}
+                "samples": len(use), "in_timed_region": bool(inside), "reasons": reasons,
+                "window": "continuous load: 0.6 s of the same steps, the K timed steps, 0.6 s more"}
 
 
 # ----------------------------------------------------------------------------- CPU oracle sample
@@ -261,13 +272,45 @@ def replica_throughput(frames_per_step: int, steps: int, world: int, ms_max: flo
     return frames_per_step * steps * world / (ms_max / 1e3)
 
 
-def run_native(args, rank, world, local_rank):
+def _measured_peaks():
+    """Measured peaks of the GB300s (MEASURED_PEAKS.json), with the recipe's
+    fallback figures where the file is missing."""
+    d = {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "source": "fallback"}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            m = json.load(f)
+        d.update({k: float(m[k]) for k in ("hbm_gbs", "sm_max_mhz") if k in m})
+        d["source"] = "measured"
+    except Exception:
+        pass
+    return d
+
+
+def _graph(fn):
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        fn()
+    return g
+
+
+def _time_replays(graphs, n, stream):
+    """Mean ms per replay of ``n`` replays cycling through ``graphs`` (CUDA events on stream)."""
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(n):
+        graphs[i % len(graphs)].replay()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / n
+
+
+def run_workload(name, args, rank, world, local_rank, *, with_e2e=True, with_clocks=True):
+    """Time one workload: K graph-replayed steps (the value), the stages alone, e2e."""
     import paper_1811_01566_gb300 as wf
-    from synth import configs  # noqa: F401
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
-    case = make_case(args.workload, str(dev))
+    case = make_case(name, str(dev))
     pr = wf.Probe(case.n_elements, case.pitch, case.fs, case.c, case.f_number, case.apod)
     gr = wf.Grid(case.nz, case.nx, case.x_min, case.x_max, case.z_min, case.z_max)
     b = case.batch
@@ -285,12 +328,16 @@ def run_native(args, rank, world, local_rank):
         scan = dict(tx_elem=case.tx_elem, t_start=case.t_start, rf_scale=case.rf_scale)
         das = wf.das_stai
     else:
-        scan = dict(angles=case.angles, t_start=case.t_starts, rf_scale=case.rf_scale)
+        scan = dict(angles=np.asarray(case.angles, np.float64),
+                    t_start=np.asarray(case.t_starts, np.float64), rf_scale=case.rf_scale)
         das = wf.das_pwi
     stream = torch.cuda.current_stream(dev)
 
-    def step(i):
+    def das_call(i):
         das(bufs[i % n_bufs], pr, gr, out=bf, workspace=ws, **scan)
+
+    def step(i):
+        das_call(i)
         wf.envelope(bf, out=env, frame_max=fmax)
         wf.logclip(env, ref=fmax, out=db)
 
@@ -304,79 +351,197 @@ def run_native(args, rank, world, local_rank):
         torch.cuda.synchronize(dev)
         return None
 
-    graphs = None
-    if not args.no_graph:
-        try:
-            graphs = []
-            for i in range(n_bufs):
-                g = torch.cuda.CUDAGraph()
-                with torch.cuda.graph(g):
-                    step(i)
-                graphs.append(g)
-            for g in graphs:
-                g.replay()
-            torch.cuda.synchronize(dev)
-        except Exception as exc:  # pragma: no cover - capture problems fall back to eager
-            print(f"# graph capture unavailable ({exc}); timing eager launches", file=sys.stderr)
-            graphs = None
+    graphs = None if args.no_graph else [_graph(lambda i=i: step(i)) for i in range(n_bufs)]
+    if graphs is not None:
+        for g in graphs:
+            g.replay()
+        torch.cuda.synchronize(dev)
+
+    def run_steps(n, offset=0):
+        for i in range(n):
+            graphs[(offset + i) % n_bufs].replay() if graphs is not None else step(offset + i)
 
     def barrier():
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize(dev)
 
-    # ---- timed region: K steps, device events, max over ranks
-    with ClockSampler(local_rank) as clk:
-        t_end = time.time() + 1.0          # keep the GPU busy while nvidia-smi starts sampling
-        i = 0
-        while time.time() < t_end:
-            graphs[i % n_bufs].replay() if graphs is not None else step(i)
-            i += 1
-            if i % 64 == 0:
-                torch.cuda.synchronize(dev)
-        barrier()
-        w0 = time.time()
+    def busy(seconds):
+        """Replay steps for ``seconds`` of wall time; returns (steps, device ms)."""
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for i in range(args.steps):
-            if graphs is not None:
-                graphs[i % n_bufs].replay()
-            else:
-                step(i)
+        t_end, n = time.time() + seconds, 0
+        while time.time() < t_end:
+            run_steps(32, n)
+            n += 32
+            torch.cuda.synchronize(dev)
+        e1.record(stream)
+        e1.synchronize()
+        return n, e0.elapsed_time(e1)
+
+    # ---- timed region: exactly K steps between device events, max over ranks.  The clock
+    # sampler covers a continuous load window around it (0.6 s of the same steps before and
+    # after), so nvidia-smi's 100 ms samples see the clocks the timed steps ran at; the window
+    # after the K steps also gives a sustained figure over many more steps.
+    with ClockSampler(local_rank) if with_clocks else _NoClock() as clk:
+        w0 = time.time()
+        busy(0.6)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        run_steps(args.steps)
         e1.record(stream)
         barrier()
+        sus_steps, sus_ms = busy(0.6)
         clk.region(w0, time.time())
     ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
     clocks = clk.summary()
 
-    # ---- stage split (eager, events between stages on the launching stream)
-    k2 = min(args.steps, 500)
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(k2)]
+    # ---- stages alone: graphs holding only the DAS call (memset, tiled kernel, split
+    # reduction), only the envelope, only the log-clip, replayed between device events.
+    das_graphs = [_graph(lambda i=i: das_call(i)) for i in range(n_bufs)]
+    env_graph = [_graph(lambda: wf.envelope(bf, out=env, frame_max=fmax))]
+    clip_graph = [_graph(lambda: wf.logclip(env, ref=fmax, out=db))]
+    n_rep = max(20, min(2000, int(0.3 / max(ms / args.steps / 1e3, 1e-6))))
     barrier()
-    for i in range(k2):
-        ev[i][0].record(stream)
-        das(bufs[i % n_bufs], pr, gr, out=bf, workspace=ws, **scan)
-        ev[i][1].record(stream)
-        wf.envelope(bf, out=env, frame_max=fmax)
-        ev[i][2].record(stream)
-        wf.logclip(env, ref=fmax, out=db)
-        ev[i][3].record(stream)
-    barrier()
-    das_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in ev)
-    env_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in ev)
-    clip_ms = statistics.mean(e[2].elapsed_time(e[3]) for e in ev)
+    das_ms = _time_replays(das_graphs, n_rep, stream)
+    env_ms = _time_replays(env_graph, n_rep, stream)
+    clip_ms = _time_replays(clip_graph, n_rep, stream)
+    # host cost of one eager library call (planning is cached after the first call)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for i in range(20):
+        das_call(i)
+    host_us = (time.perf_counter() - t0) / 20 * 1e6
+    torch.cuda.synchronize(dev)
 
-    # ---- end to end: pinned host RF in, dB image out, every step.  As a streaming caller
-    # would, the next frame's host-to-device copy runs on a copy stream while the current
-    # frame is reconstructed (two device RF buffers, events between the streams).  The copy
-    # moves the transfer plan's boxes (planned once per scan, outside the timed region): the
-    # samples the DAS call can read, one 3D copy per group of 16 transmits.
+    e2e = None
+    if with_e2e:
+        e2e = run_e2e(wf, case, pr, gr, das, scan, rf_host, rf_dev, ws, bf, env, db, fmax, step,
+                      args, world, dev, stream, barrier)
+
+    if rank != 0:
+        return None
+    dense, active, contributing, per_px = delay_sum_counts(case, dev)
+    fps = replica_throughput(b, args.steps, world, ms)
+    props = torch.cuda.get_device_properties(dev)
+    peaks = _measured_peaks()
+    clk_mhz = peaks["sm_max_mhz"]
+    n_sm = props.multi_processor_count
+    gather_peak = n_sm * SMEM_WORDS_PER_CLOCK * clk_mhz * 1e6 / WORDS_PER_DELAY_SUM / 1e9
+    gather_achieved = active * b / (das_ms / 1e3) / 1e9
+    fp32_peak = n_sm * 128 * clk_mhz * 1e6 / 1e12
+    fp32_achieved = contributing * b * FP32_OPS_PER_DELAY_SUM / (das_ms / 1e3) / 1e12
+    px_bytes = case.nz * case.nx * b * 4
+
+    def hbm(bytes_, ms_):
+        gbs = bytes_ / (ms_ / 1e3) / 1e9
+        return {"achieved_gbs": round(gbs, 1), "frac_of_measured_hbm": round(gbs / peaks["hbm_gbs"], 4),
+                "bytes": bytes_}
+
+    line = {
+        "metric": "DAS frames/s (B-mode: delay-and-sum + envelope + log-clip per frame)",
+        "value": round(fps, 2),
+        "unit": "frames/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms / args.steps, 5),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {
+            "workload": f"{name}: {WORKLOAD_TEXT[name]}",
+            "frames_per_step": b,
+            "rf_storage": case.dtype,
+            "parallelism": "replicas" if world > 1 else "single GPU",
+            "l2": f"inputs larger than L2: {n_bufs} rotating RF copies "
+                  f"({n_bufs * rf_bytes / 2**20:.0f} MiB > 129 MB L2)",
+            "launch": "CUDA graph per step" if graphs is not None else "eager launches",
+        },
+        "sustained": {"value": round(replica_throughput(b, sus_steps, 1, sus_ms), 2),
+                      "unit": "frames/s", "steps": sus_steps, "seconds": round(sus_ms / 1e3, 3),
+                      "note": "the same graph-replayed steps over the 0.6 s after the timed ones"},
+        "delay_sums_per_frame": {"dense": dense, "aperture_active": active,
+                                 "contributing": contributing},
+        "g_delay_sums_per_s": {
+            "aperture_active": round(gather_achieved, 2),
+            "contributing": round(contributing * b / (das_ms / 1e3) / 1e9, 2),
+            "dense": round(dense * b / (das_ms / 1e3) / 1e9, 2)},
+        "stages_ms": {"das": round(das_ms, 5), "envelope": round(env_ms, 5),
+                      "logclip": round(clip_ms, 5),
+                      "basis": "CUDA events around replays of a graph holding only that stage"},
+        "host_us_per_das_call": round(host_us, 1),
+        "roofline": {
+            "kernel": f"das_tiled_kernel + split reduction ({'wf_das_stai' if case.mode == 'stai' else 'wf_das_pwi'})",
+            "bound": "smem_gather",
+            "achieved": round(gather_achieved, 2),
+            "peak": round(gather_peak, 2),
+            "unit": "G delay-sums/s",
+            "frac": round(gather_achieved / gather_peak, 4),
+            "traffic": ncu_traffic(name),
+            "peak_basis": f"{n_sm} SMs x {SMEM_WORDS_PER_CLOCK} shared-memory words/clock x "
+                          f"{clk_mhz:.0f} MHz ({peaks['source']} max SM clock) / "
+                          f"{WORDS_PER_DELAY_SUM} words (one FP32 pair) per delay-sum",
+            "algorithmic": f"{active} aperture-active delay-sums per frame (both apodization "
+                           f"weights non-zero) x {b} frames per launch",
+            "time_basis": "DAS call alone (memset + tiled kernel + reduction) from graph replays",
+            "fp32": {"achieved_tops": round(fp32_achieved, 3), "peak_tops": round(fp32_peak, 3),
+                     "frac": round(fp32_achieved / fp32_peak, 4),
+                     "basis": f"{FP32_OPS_PER_DELAY_SUM} FP32 ops x {contributing} contributing "
+                              f"delay-sums per frame; {n_sm} SMs x 128 lanes x {clk_mhz:.0f} MHz"},
+            "contributing_frac": round(contributing * b / (das_ms / 1e3) / 1e9 / gather_peak, 4),
+        },
+        "stage_rooflines": {
+            "envelope": hbm(2 * px_bytes, env_ms),
+            "logclip": hbm(2 * px_bytes, clip_ms),
+            "basis": f"8 B per pixel (read + write float32) against the measured "
+                     f"{peaks['hbm_gbs']:.0f} GB/s copy bandwidth",
+        },
+        "gpu_launches": 4 * args.steps,
+        "clocks": clocks,
+    }
+    if e2e is not None:
+        line["e2e"] = e2e
+    line["_case"] = case
+    line["_per_px"] = per_px
+    return line
+
+
+class _NoClock:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        return False
+
+    def region(self, t0, t1):
+        pass
+
+    def summary(self):
+        return None
+
+
+def run_e2e(wf, case, pr, gr, das, scan, rf_host, rf_dev, ws, bf, env, db, fmax, step, args,
+            world, dev, stream, barrier):
+    """End to end through the library calls: pinned host RF in, dB image out, every step.
+
+    As a streaming caller would, the next frame's host-to-device copy runs on a copy stream
+    while the current frame is reconstructed (two device RF buffers, events between the
+    streams).  The copy moves the transfer plan's boxes (planned once per scan, outside the
+    timed region): the samples the DAS call can read, one 3D copy per group of 16 transmits.
+    """
+    b = case.batch
+    rf_bytes = rf_dev.numel() * rf_dev.element_size()
     plan_scan = (dict(tx_elem=case.tx_elem, t_start=case.t_start) if case.mode == "stai"
                  else dict(angles=case.angles, t_start=case.t_starts))
     boxes = wf.rf_boxes(pr, gr, case.mode, n_tx=case.n_tx, n_samples=case.n_samples,
                         dtype=rf_host.dtype, group=16, **plan_scan)
     box_bytes = b * rf_host.element_size() * sum(
         (t1 - t0) * (r1 - r0) * (s1 - s0) for t0, t1, r0, r1, s0, s1 in boxes)
+    copy_stream = torch.cuda.Stream(dev)
 
     def copy_in(dst):
         for f in range(b):
@@ -384,10 +549,9 @@ def run_native(args, rank, world, local_rank):
 
     db_host = [torch.empty(db.shape, dtype=db.dtype, pin_memory=True) for _ in range(2)]
     rf_in = [torch.zeros_like(rf_dev) for _ in range(2)]   # nothing outside the boxes arrives
-    copy_stream = torch.cuda.Stream(dev)
     copied = [torch.cuda.Event() for _ in range(2)]
     done = [torch.cuda.Event() for _ in range(2)]
-    k3 = min(args.steps, 200)
+    k3 = max(args.steps, 100)
     barrier()
     t0 = time.perf_counter()
     x0 = torch.cuda.Event(enable_timing=True)
@@ -423,82 +587,38 @@ def run_native(args, rank, world, local_rank):
     torch.cuda.synchronize(dev)
     if not torch.equal(db, db_e2e):
         raise RuntimeError("the transfer plan left out samples the DAS call read")
+    return {"value": round(replica_throughput(b, 1, world, e2e_ms), 2), "unit": "frames/s",
+            "h2d_bytes_per_step": box_bytes, "d2h_bytes_per_step": db.numel() * 4,
+            "steps": k3, "wall_ms_per_step": round(wall_e2e, 4),
+            "transfer": f"rf_boxes plan: {len(boxes)} boxes per frame, {box_bytes // b} of "
+                        f"{rf_bytes // b} RF bytes (the samples the DAS call can read)",
+            "pipelining": "next frame's pinned H2D copy on a copy stream overlaps the current "
+                          "frame's kernels; every step copies its RF in and its dB image out"}
 
-    if rank != 0:
-        return None
-    dense, active, contributing, per_px = delay_sum_counts(case, dev)
-    fps = replica_throughput(b, args.steps, world, ms)
-    props = torch.cuda.get_device_properties(dev)
-    peak_mhz = 2070.0
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            peak_mhz = float(json.load(f).get("sm_max_mhz", peak_mhz))
-    except Exception:
-        pass
-    peak_tops = props.multi_processor_count * 128 * peak_mhz * 1e6 / 1e12
-    achieved_tops = contributing * b * FP32_OPS_PER_DELAY_SUM / (das_ms / 1e3) / 1e12
-    line = {
-        "metric": "DAS frames/s (B-mode: delay-and-sum + envelope + log-clip per frame)",
-        "value": round(fps, 2),
-        "unit": "frames/s",
-        "n_gpus": world,
-        "steps": args.steps,
-        "warmup": args.warmup,
-        "ms_per_step": round(ms / args.steps, 5),
-        "higher_is_better": True,
-        "scaling": "weak",
-        "vs_baseline": None,
-        "dtype": "f32",
-        "data": "synthetic",
-        "config": {
-            "workload": f"{args.workload}: {WORKLOAD_TEXT[args.workload]}",
-            "frames_per_step": b,
-            "rf_storage": case.dtype,
-            "parallelism": "replicas" if world > 1 else "single GPU",
-            "l2": f"inputs larger than L2: {n_bufs} rotating RF copies "
-                  f"({n_bufs * rf_bytes / 2**20:.0f} MiB > 129 MB L2)",
-            "launch": "CUDA graph per step" if graphs is not None else "eager launches",
-        },
-        "delay_sums_per_frame": {"dense": dense, "aperture_active": active,
-                                 "contributing": contributing},
-        "g_delay_sums_per_s": {
-            "contributing": round(contributing * b / (das_ms / 1e3) / 1e9, 2),
-            "aperture_active": round(active * b / (das_ms / 1e3) / 1e9, 2),
-            "dense": round(dense * b / (das_ms / 1e3) / 1e9, 2)},
-        "stages_ms": {"das": round(das_ms, 5), "envelope": round(env_ms, 5),
-                      "logclip": round(clip_ms, 5)},
-        "roofline": {
-            "kernel": "wf_das_stai (tiled DAS + split reduction)" if case.mode == "stai"
-                      else "wf_das_pwi (tiled DAS + split reduction)",
-            "bound": "alu",
-            "achieved": round(achieved_tops, 3),
-            "peak": round(peak_tops, 3),
-            "unit": "Top/s (FP32 lane ops)",
-            "frac": round(achieved_tops / peak_tops, 4),
-            "traffic": ncu_traffic(args.workload),
-            "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {peak_mhz:.0f} MHz "
-                          f"(derived from unit counts and max clock)",
-            "algorithmic": f"{FP32_OPS_PER_DELAY_SUM} FP32 ops x {contributing} contributing "
-                           f"delay-sums per frame",
-        },
-        "e2e": {"value": round(replica_throughput(b, 1, world, e2e_ms), 2), "unit": "frames/s",
-                "h2d_bytes_per_step": box_bytes, "d2h_bytes_per_step": db.numel() * 4,
-                "wall_ms_per_step": round(wall_e2e, 4),
-                "transfer": f"rf_boxes plan: {len(boxes)} boxes per frame, {box_bytes // b} of "
-                            f"{rf_bytes // b} RF bytes (the samples the DAS call can read)",
-                "pipelining": "next frame's pinned H2D copy on a copy stream overlaps the current "
-                              "frame's kernels; every step copies its RF in and its dB image out"},
-        "gpu_launches": 4 * args.steps,
-        "clocks": clocks,
-    }
-    if not args.no_cpu_baseline:
-        cpu_case = case if case.batch == 1 else None
-        if cpu_case is not None:
-            v, desc, spent, _ = oracle_sample(case, args.cpu_seconds, per_px)
-            line["cpu_baseline"] = {"value": round(v, 6), "unit": "frames/s", "cores": 1,
-                                    "kind": "oracle", "sample": desc,
-                                    "cpu": _cpu_model(), "seconds": round(spent, 2)}
-    return line
+
+def oracle_frame_nproc(case, threads=None):
+    """One full frame of the FP64 oracle (DAS + envelope + log-clip), image rows split over
+    ``threads`` host threads in interleaved bands of 8 rows (ctypes releases the GIL).
+    Returns (seconds, threads)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import oracle
+    threads = threads or os.cpu_count() or 1
+    pr, gr = oracle.probe_grid(case)
+    rf = case.rf64[0]
+    bands = [(r, min(case.nz, r + 8)) for r in range(0, case.nz, 8)]
+    bands.sort(key=lambda ab: -ab[0])            # deep rows carry the widest apertures: first
+
+    def band(ab):
+        if case.mode == "stai":
+            return oracle.das_stai(rf, pr, gr, tx_elem=case.tx_elem, t_start=case.t_start, rows=ab)
+        return oracle.das_pwi(rf, pr, gr, angles=case.angles, t_starts=case.t_starts, rows=ab)
+
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(threads) as ex:
+        img = sum(ex.map(band, bands))
+    oracle.logclip(oracle.envelope(img, threads=threads))
+    return time.perf_counter() - t0, threads
 
 
 def ncu_traffic(workload):
@@ -521,14 +641,27 @@ def ncu_traffic(workload):
 
 
 def _cpu_model():
+    """CPU model and logical core count of the host (lscpu's model name where it has one:
+    Arm hosts list only part numbers in /proc/cpuinfo)."""
+    name = None
     try:
-        with open("/proc/cpuinfo") as f:
-            for ln in f:
-                if ln.lower().startswith(("model name", "cpu part", "hardware")):
-                    return ln.split(":", 1)[1].strip()
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.split(":", 1)[0].strip() in ("Model name", "Vendor ID") and ":" in ln:
+                v = ln.split(":", 1)[1].strip()
+                name = v if name is None else f"{name} {v}" if v not in name else name
     except Exception:
         pass
-    return os.uname().machine
+    if not name:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for ln in f:
+                    if ln.lower().startswith(("model name", "cpu part", "hardware")):
+                        name = ln.split(":", 1)[1].strip()
+                        break
+        except Exception:
+            pass
+    return f"{name or os.uname().machine}, {os.cpu_count()} logical cores"
 
 
 # ----------------------------------------------------------------------------- served stream
@@ -688,23 +821,39 @@ def run_diff(args):
 # ----------------------------------------------------------------------------- reference arm
 
 def run_reference(args):
-    """The FP64 CPU oracle, timed on host cores on bounded samples of the same workload."""
+    """The FP64 CPU oracle, timed on the host cores on the same workload.
+
+    Each timed step is one full frame (DAS, envelope, log-clip) with the image rows split
+    over every host core, so ``ms_per_step`` is a measured frame time, not an
+    extrapolation; warm-up steps run one 8-row band.  Should K full frames project past
+    ~200 s, the remaining steps time an evenly spaced eighth of the rows each and are
+    scaled by their share of the frame's contributing delay-sums (reported)."""
     dev = "cuda" if torch.cuda.is_available() else None
     case = make_case(args.workload, dev)
-    counts = delay_sum_counts(case, dev or "cpu")[3]
-    # the whole run stays near two minutes whatever K is: each step is a bounded sample
-    per_step = min(args.cpu_seconds, 100.0 / max(1, args.steps + args.warmup))
-    spent, t_das, frac, t_post = 0.0, 0.0, 0.0, []
-    desc = ""
-    for i in range(args.warmup + args.steps):
-        _, desc, s, parts = oracle_sample(case, per_step, counts, start=7 * i)
-        if i >= args.warmup:
-            spent += s
-            t_das += parts[0]
-            frac += parts[1]
-            t_post.append(parts[2])
-    # pooled over the steps (ratio of sums): DAS seconds per frame + post-processing seconds
-    fps = 1.0 / (t_das / max(frac, 1e-12) + statistics.mean(t_post))
+    threads = os.cpu_count() or 1
+    counts = None
+    for _ in range(args.warmup):
+        oracle_rows(case, [(case.nz // 2, min(case.nz, case.nz // 2 + 8))], threads)
+    times, sampled = [], 0
+    t_run0 = time.perf_counter()
+    for i in range(args.steps):
+        if times and statistics.mean(times) * args.steps > 200.0 and i >= 1:
+            if counts is None:
+                counts = delay_sum_counts(case, dev or "cpu")[3].sum(axis=1)
+            rows = [(r, min(case.nz, r + 8)) for r in range(8 * (i % 8), case.nz, 64)]
+            sec = oracle_rows(case, rows, threads)
+            frac = sum(float(counts[a:b_].sum()) for a, b_ in rows) / max(float(counts.sum()), 1.0)
+            times.append(sec / max(frac, 1e-9))
+            sampled += 1
+        else:
+            sec, _ = oracle_frame_nproc(case, threads)
+            times.append(sec)
+    wall = time.perf_counter() - t_run0
+    frame_s = statistics.mean(times)
+    fps = 1.0 / frame_s
+    desc = (f"full frames ({args.steps - sampled} of {args.steps} steps; {sampled} sampled steps "
+            f"scaled by their contributing delay-sums), image rows in 8-row bands over {threads} "
+            f"threads")
     line = {
         "impl": "reference",
         "metric": "DAS frames/s (B-mode: delay-and-sum + envelope + log-clip per frame)",
@@ -713,21 +862,60 @@ def run_reference(args):
         "n_gpus": 1,
         "steps": args.steps,
         "warmup": args.warmup,
-        "ms_per_step": round(1e3 / fps, 3),
+        "ms_per_step": round(wall / max(args.steps, 1) * 1e3, 3),
+        "frame_ms": round(frame_s * 1e3, 3),
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": f"{args.workload}: {WORKLOAD_TEXT[args.workload]}",
-                   "frames_per_step": 1, "parallelism": "single CPU thread"},
-        "cpu_baseline": {"value": round(fps, 6), "unit": "frames/s", "cores": 1, "kind": "oracle",
-                         "sample": f"per step, {desc}; pooled over {args.steps} steps",
-                         "cpu": _cpu_model(), "seconds": round(spent, 2)},
+                   "frames_per_step": 1, "parallelism": f"{threads} CPU threads"},
+        "cpu_baseline": {"value": round(fps, 6), "unit": "frames/s", "cores": threads,
+                         "kind": "oracle", "sample": desc, "cpu": _cpu_model(),
+                         "seconds": round(wall, 2)},
         "e2e": {"value": round(fps, 6), "unit": "frames/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
     return line
+
+
+def oracle_rows(case, rows, threads):
+    """Seconds of the oracle's DAS over the given row bands on ``threads`` threads."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import oracle
+    pr, gr = oracle.probe_grid(case)
+    rf = case.rf64[0]
+
+    def band(ab):
+        if case.mode == "stai":
+            return oracle.das_stai(rf, pr, gr, tx_elem=case.tx_elem, t_start=case.t_start, rows=ab)
+        return oracle.das_pwi(rf, pr, gr, angles=case.angles, t_starts=case.t_starts, rows=ab)
+
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(threads) as ex:
+        list(ex.map(band, rows))
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(case, per_px, args):
+    """The oracle on the host cores: one full frame over every core (timed) and a bounded
+    single-thread sample (scaled to a frame)."""
+    sec, threads = oracle_frame_nproc(case)
+    v1, desc1, spent1, _ = oracle_sample(case, args.cpu_seconds, per_px)
+    return {"value": round(1.0 / sec, 6), "unit": "frames/s", "cores": threads, "kind": "oracle",
+            "sample": f"one full frame (DAS + envelope + log-clip), image rows in 8-row bands "
+                      f"over {threads} threads, timed whole",
+            "cpu": _cpu_model(), "seconds": round(sec, 2),
+            "single_thread": {"value": round(v1, 6), "unit": "frames/s", "cores": 1,
+                              "sample": desc1, "seconds": round(spent1, 2)}}
+
+
+def _summary(line):
+    keep = ("value", "ms_per_step", "config", "delay_sums_per_frame", "g_delay_sums_per_s",
+            "stages_ms", "host_us_per_das_call", "roofline", "stage_rooflines", "e2e", "sustained")
+    return {k: line[k] for k in keep if k in line}
 
 
 def main():
@@ -754,7 +942,23 @@ def main():
     if world > 1:
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     try:
-        line = run_native(args, rank, world, local_rank)
+        line = run_workload(args.workload, args, rank, world, local_rank)
+        if line is not None and not args.profile_only:
+            case, per_px = line.pop("_case"), line.pop("_per_px")
+            if not args.no_cpu_baseline and case.batch == 1 and world == 1:
+                line["cpu_baseline"] = cpu_baseline(case, per_px, args)
+            del case
+        if not args.profile_only and not args.no_extra and args.workload == DEFAULT_WORKLOAD:
+            extra = {}
+            for name in EXTRA_WORKLOADS:
+                torch.cuda.empty_cache()
+                x = run_workload(name, args, rank, world, local_rank,
+                                 with_e2e=(name == "stai_full"), with_clocks=False)
+                if x is not None:
+                    x.pop("_case"), x.pop("_per_px")
+                    extra[name] = _summary(x)
+            if line is not None:
+                line["extra"] = extra
         if rank == 0 and line is not None:
             print(json.dumps(line), flush=True)
     finally:

@@ -411,6 +411,30 @@ wf_status wf_fixed_scratch_check(wf_stream stream);
  */
 wf_status wf_das_reload_tuning(void);
 
+/* What a DAS call with these arguments runs (diagnostics; host only). */
+typedef struct {
+    int32_t tiled;            /* 1: tiled gather kernels; 0: the per-pixel path */
+    int32_t tile_cols;        /* pixel tile of a CTA (columns x rows) */
+    int32_t tile_rows;
+    int32_t window;           /* staged samples per trace (shared-memory stride) */
+    int32_t ring;             /* bulk-copy ring depth (0: register-staged or per-pixel) */
+    int32_t reciprocal;       /* STAI: reciprocal (t, r) / (r, t) pairing in use */
+    int32_t ctas_per_frame;   /* tiled: CTAs the schedule launches for the whole batch */
+    int32_t smem_bytes;       /* tiled forward: dynamic shared memory per CTA */
+    int64_t workspace_bytes;  /* forward: workspace this call needs */
+} wf_das_plan_info;
+
+/*
+ * Plan of wf_das_stai (mode 0) / wf_das_pwi (mode 1) -- reverse = 0 -- or of
+ * wf_das_backward -- reverse = 1 -- for these arguments (as those calls;
+ * t_start NULL means 0), written to *info.  The forward plan is the cached one
+ * the call itself uses.
+ */
+wf_status wf_das_plan(const wf_probe* probe, const wf_grid* grid, int32_t mode, int32_t reverse,
+                      int32_t batch, int32_t n_tx, const int32_t* tx_elem, const double* angles_rad,
+                      const double* t_start, int32_t n_samples, wf_dtype dtype,
+                      wf_das_plan_info* info);
+
 /*
  * Synchronises `stream` and reports whether a DAS kernel that used `ws`
  * recorded an internal inconsistency (WF_ERR_INTERNAL) since the workspace

@@ -15,6 +15,7 @@ import ctypes as C
 import dataclasses
 import os
 import threading
+import weakref
 from dataclasses import dataclass
 
 import torch
@@ -25,7 +26,7 @@ __all__ = ["Probe", "Grid", "WfError", "HANN", "RECT", "NONE", "das_stai", "das_
            "das_workspace_bytes", "das_delays", "das_backward", "das", "envelope", "logclip",
            "envelope_backward", "logclip_backward", "bmode", "bmode_diff", "fir", "iq_demod",
            "fir_bandpass", "workspace_check", "rf_boxes", "copy_rf_boxes", "library_path",
-           "version", "reload_tuning"]
+           "version", "reload_tuning", "das_plan"]
 
 HANN, RECT, NONE = 0, 1, 2
 _DTYPES = {torch.float32: 0, torch.float16: 1, torch.int16: 2}
@@ -50,6 +51,13 @@ class _WfProbe(C.Structure):
 class _WfGrid(C.Structure):
     _fields_ = [("nz", C.c_int32), ("nx", C.c_int32), ("x_min", C.c_double),
                 ("x_max", C.c_double), ("z_min", C.c_double), ("z_max", C.c_double)]
+
+
+class _WfPlanInfo(C.Structure):
+    _fields_ = [("tiled", C.c_int32), ("tile_cols", C.c_int32), ("tile_rows", C.c_int32),
+                ("window", C.c_int32), ("ring", C.c_int32), ("reciprocal", C.c_int32),
+                ("ctas_per_frame", C.c_int32), ("smem_bytes", C.c_int32),
+                ("workspace_bytes", C.c_int64)]
 
 
 class _WfRfBox(C.Structure):
@@ -108,6 +116,9 @@ def _load():
             lib.wf_das_rf_boxes.restype = C.c_int
             lib.wf_copy_rf_boxes.argtypes = [vp, vp, i32, i32, i32, i32, vp, i32, vp]
             lib.wf_copy_rf_boxes.restype = C.c_int
+            lib.wf_das_plan.argtypes = [P, G, i32, i32, i32, i32, vp, vp, vp, i32, i32,
+                                        C.POINTER(_WfPlanInfo)]
+            lib.wf_das_plan.restype = C.c_int
             lib.wf_das_reload_tuning.argtypes = []
             lib.wf_das_reload_tuning.restype = C.c_int
             lib.wf_workspace_check.argtypes = [vp, sz, vp]
@@ -206,6 +217,20 @@ def _f64_array(values, n: int):
     if a.size != n:
         raise ValueError(f"expected {n} values, got {a.size}")
     return (C.c_double * n).from_buffer_copy(a.data)
+
+
+def das_plan(probe: Probe, grid: Grid, mode: str, *, n_tx: int, n_samples: int,
+             dtype: torch.dtype = torch.float32, batch: int = 1, reverse: bool = False,
+             tx_elem=None, angles=None, t_start=None) -> dict:
+    """What wf_das_stai / wf_das_pwi (or, reverse, wf_das_backward) runs for these arguments."""
+    if mode not in ("stai", "pwi"):
+        raise ValueError("mode must be 'stai' or 'pwi'")
+    tx, ang, ts = _scan_args(mode, n_tx, tx_elem, angles, t_start)
+    info = _WfPlanInfo()
+    _check(_load().wf_das_plan(C.byref(probe._c()), C.byref(grid._c()), 0 if mode == "stai" else 1,
+                               int(bool(reverse)), int(batch), int(n_tx), tx, ang, ts, int(n_samples),
+                               _DTYPES[dtype], C.byref(info)), "wf_das_plan")
+    return {n: getattr(info, n) for n, _ in _WfPlanInfo._fields_}
 
 
 def reload_tuning() -> None:
@@ -372,12 +397,36 @@ def das_backward(rf: torch.Tensor, grad_out: torch.Tensor, probe: Probe, grid: G
     return grf, gw, gc
 
 
+_C_VALUES = weakref.WeakKeyDictionary()   # sound-speed tensor -> (version, host value)
+
+
+def _host_scalar(c) -> float:
+    """Host value of a scalar tensor, read from the device only when the tensor is new or has
+    been modified in place since the last read (its version counter moved): the library plans
+    a call's geometry on the host, and re-reading an unchanged value every step would
+    synchronise the host with the device each time.  (A value swapped in through ``.data``
+    does not move the counter: assign through in-place operations.)"""
+    if not isinstance(c, torch.Tensor):
+        return float(c)
+    d = c.detach()
+    ver = c._version
+    hit = _C_VALUES.get(c)
+    if hit is not None and hit[0] == ver:
+        return hit[1]
+    val = float(d.reshape(()).item())
+    try:
+        _C_VALUES[c] = (ver, val)
+    except TypeError:
+        pass
+    return val
+
+
 class _DelayAndSum(torch.autograd.Function):
     """DAS as an autograd node: forward wf_das_stai / wf_das_pwi, backward wf_das_backward."""
 
     @staticmethod
     def forward(ctx, rf, elem_weight, c, probe, grid, mode, scan):
-        cval = float(c.detach().reshape(()).item()) if isinstance(c, torch.Tensor) else float(c)
+        cval = _host_scalar(c)
         w = None if elem_weight is None else elem_weight.detach().contiguous()
         p = dataclasses.replace(probe, c=cval, elem_weight=w)
         fwd = das_stai if mode == "stai" else das_pwi

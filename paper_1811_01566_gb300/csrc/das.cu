@@ -507,6 +507,10 @@ std::string plan_key(int mode, const wf_probe* p, const wf_grid* g, int batch, i
     return k.s;
 }
 
+wf_status get_plan(int mode, const wf_probe* probe, const wf_grid* grid, int32_t batch, int32_t n_tx,
+                   const int32_t* tx_elem, const double* angles, const double* t_start,
+                   int32_t n_samples, wf_dtype dtype, std::shared_ptr<const CachedPlan>& out);
+
 // The delay-and-sum call of both transmit schemes: host checks, cached plan, launch.
 // STAI passes tx_elem and t_start[0]; PWI passes angles and t_start[n_tx] (or NULL).
 wf_status das_run(int mode, const wf_probe* probe, const wf_grid* grid, int32_t batch,
@@ -525,6 +529,30 @@ wf_status das_run(int mode, const wf_probe* probe, const wf_grid* grid, int32_t 
     if (dtype == WF_I16 && !std::isfinite(rf_scale)) return WF_ERR_INVALID_ARG;
     if (!rf || !out) return WF_ERR_INVALID_ARG;
     if (((uintptr_t)rf & 15u) || ((uintptr_t)out & 3u)) return WF_ERR_INVALID_ARG;
+    std::shared_ptr<const CachedPlan> e;
+    if ((s = get_plan(mode, probe, grid, batch, n_tx, tx_elem, angles, t_start, n_samples, dtype, e)) !=
+        WF_OK)
+        return s;
+    const Plan& P = e->P;
+    if (!ws || ((uintptr_t)ws & 15u)) return WF_ERR_WORKSPACE;
+    if (ws_bytes < P.ws_bytes) return WF_ERR_WORKSPACE;
+    A = *e->A;
+    A.g.elem_weight = probe->elem_weight;
+    A.rf = rf;
+    A.rf_scale = dtype == WF_I16 ? rf_scale : 1.0f;
+    A.hdr = static_cast<WsHeader*>(ws);
+    A.tile_info = reinterpret_cast<unsigned*>(static_cast<char*>(ws) + kWsHeaderBytes);
+    A.part = reinterpret_cast<float*>(static_cast<char*>(ws) + kWsHeaderBytes + P.info_bytes);
+    A.out = out;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if ((s = cuda_status(cudaMemsetAsync(ws, 0, kWsHeaderBytes + P.info_bytes, st))) != WF_OK) return s;
+    return mode == 0 ? dispatch<0>(A, P, batch, dtype, st) : dispatch<1>(A, P, batch, dtype, st);
+}
+
+// The cached plan of a call (built on a miss); arguments as das_run, already range-checked.
+wf_status get_plan(int mode, const wf_probe* probe, const wf_grid* grid, int32_t batch, int32_t n_tx,
+                   const int32_t* tx_elem, const double* angles, const double* t_start,
+                   int32_t n_samples, wf_dtype dtype, std::shared_ptr<const CachedPlan>& out) {
     const Tuning tu = tuning();
     const std::string key =
         plan_key(mode, probe, grid, batch, n_tx, tx_elem, angles, t_start, n_samples, dtype, tu.gen);
@@ -560,20 +588,8 @@ wf_status das_run(int mode, const wf_probe* probe, const wf_grid* grid, int32_t 
         g_plans.put(key, ne);
         e = ne;
     }
-    const Plan& P = e->P;
-    if (!ws || ((uintptr_t)ws & 15u)) return WF_ERR_WORKSPACE;
-    if (ws_bytes < P.ws_bytes) return WF_ERR_WORKSPACE;
-    A = *e->A;
-    A.g.elem_weight = probe->elem_weight;
-    A.rf = rf;
-    A.rf_scale = dtype == WF_I16 ? rf_scale : 1.0f;
-    A.hdr = static_cast<WsHeader*>(ws);
-    A.tile_info = reinterpret_cast<unsigned*>(static_cast<char*>(ws) + kWsHeaderBytes);
-    A.part = reinterpret_cast<float*>(static_cast<char*>(ws) + kWsHeaderBytes + P.info_bytes);
-    A.out = out;
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    if ((s = cuda_status(cudaMemsetAsync(ws, 0, kWsHeaderBytes + P.info_bytes, st))) != WF_OK) return s;
-    return mode == 0 ? dispatch<0>(A, P, batch, dtype, st) : dispatch<1>(A, P, batch, dtype, st);
+    out = e;
+    return WF_OK;
 }
 
 // Fill the transmit table; returns the largest |t0 fs| (samples) or -1 on bad input.
@@ -854,6 +870,52 @@ extern "C" wf_status wf_das_pwi(const wf_probe* probe, const wf_grid* grid, int3
     if (!probe || !angles_rad) return WF_ERR_INVALID_ARG;
     return das_run(1, probe, grid, batch, n_angles, nullptr, angles_rad, t_start, n_rx, n_samples,
                    dtype, rf, rf_scale, out, ws, ws_bytes, stream);
+}
+
+extern "C" wf_status wf_das_plan(const wf_probe* probe, const wf_grid* grid, int32_t mode,
+                                 int32_t reverse, int32_t batch, int32_t n_tx, const int32_t* tx_elem,
+                                 const double* angles_rad, const double* t_start, int32_t n_samples,
+                                 wf_dtype dtype, wf_das_plan_info* info) {
+    if (!info || (mode != 0 && mode != 1) || (mode == 1 && !angles_rad)) return WF_ERR_INVALID_ARG;
+    wf_status s = check_probe_grid(probe, grid);
+    if (s != WF_OK) return s;
+    if (batch < 1 || batch > 65535 || n_tx < 1 || n_tx > WF_MAX_TX) return WF_ERR_INVALID_ARG;
+    if (n_samples < 1 || n_samples > WF_MAX_SAMPLES) return WF_ERR_INVALID_ARG;
+    if (dtype != WF_F32 && dtype != WF_F16 && dtype != WF_I16) return WF_ERR_INVALID_ARG;
+    const double t0 = 0.0;
+    const double* ts = mode == 0 ? (t_start ? t_start : &t0) : t_start;
+    std::memset(info, 0, sizeof(*info));
+    if (reverse) {
+        thread_local DasArgs a;
+        const double extra = fill_tx(a, probe, mode, n_tx, tx_elem, angles_rad, ts, mode == 1);
+        if (extra < 0.0) return WF_ERR_INVALID_ARG;
+        GeomD D;
+        make_geom(probe, grid, a.g, D);
+        const bool sym = use_sym(mode, n_tx, probe->n_elements, tx_elem);
+        const Plan P = plan_for(mode, Cfg{4, 2}, D, probe, grid, batch, n_tx, n_samples, 4, sym);
+        info->tiled = backward_is_tiled(P, probe->n_elements, true) ? 1 : 0;
+        info->tile_cols = P.cols;
+        info->tile_rows = P.rows;
+        info->window = P.W;
+        info->reciprocal = P.sym ? 1 : 0;
+        info->ctas_per_frame = info->tiled ? P.n_items : 0;
+        return WF_OK;
+    }
+    std::shared_ptr<const CachedPlan> e;
+    if ((s = get_plan(mode, probe, grid, batch, n_tx, tx_elem, angles_rad, ts, n_samples, dtype, e)) !=
+        WF_OK)
+        return s;
+    const Plan& P = e->P;
+    info->tiled = P.tiled ? 1 : 0;
+    info->tile_cols = P.cols;
+    info->tile_rows = P.rows;
+    info->window = P.W;
+    info->ring = P.tiled && P.tma ? P.ring : 0;
+    info->reciprocal = P.sym ? 1 : 0;
+    info->ctas_per_frame = P.tiled ? e->A->n_items : 0;
+    info->smem_bytes = P.tiled ? (int32_t)P.smem : 0;
+    info->workspace_bytes = (int64_t)P.ws_bytes;
+    return WF_OK;
 }
 
 extern "C" wf_status wf_das_reload_tuning(void) {

@@ -518,12 +518,16 @@ wf_status launch_bwd_need(DasArgs& A, const Plan& P, int batch, bool need_rf, bo
     return launch_bwd_v<MODE, SYM, false, true>(A, P, batch, st);
 }
 
+bool backward_is_tiled(const Plan& P, int n_elements, bool need_rf) {
+    return P.tiled && bwd_smem_layout(P.W, n_elements, need_rf).total <= kMaxTiledSmem;
+}
+
 template <int MODE>
 wf_status launch_das_backward(DasArgs& A, const Plan& P, int batch, bool need_rf, bool need_par,
                               cudaStream_t st) {
     if (P.cfg.wcol != kBwdWCOL || P.cfg.p != kBwdP) return WF_ERR_UNSUPPORTED;
     if (!need_rf && !need_par) return WF_OK;
-    if (!P.tiled || bwd_smem_layout(A.W, A.g.n_elements, need_rf).total > kMaxTiledSmem) {
+    if (!backward_is_tiled(P, A.g.n_elements, need_rf)) {
         dim3 grid((A.g.nx + 31) / 32, (A.g.nz + 7) / 8, batch);
         das_backward_direct_kernel<MODE><<<grid, 256, 0, st>>>(A);
         return last_launch_status();

@@ -1151,6 +1151,9 @@ template <int MODE>
 wf_status launch_das_backward(DasArgs& A, const Plan& P, int batch, bool need_rf, bool need_par,
                               cudaStream_t st);
 
+// Whether the reverse-mode launcher takes the tiled kernel for this plan (das_grad.cu).
+bool backward_is_tiled(const Plan& P, int n_elements, bool need_rf);
+
 // Tiled launch of one mode and bounds-check variant, every RF type.
 template <int MODE, bool CHECK>
 wf_status launch_das_tiled(DasArgs& A, const Plan& P, int batch, wf_dtype dt, cudaStream_t st) {

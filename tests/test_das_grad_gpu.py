@@ -8,6 +8,8 @@ pins those to the forward by the adjoint identity and finite differences):
 plus the adjoint identity of the GPU forward and backward themselves, central
 finite differences of the GPU forward, and the torch.autograd.Function.
 """
+from dataclasses import replace as dc_replace
+
 import numpy as np
 import pytest
 import torch
@@ -73,6 +75,76 @@ def test_backward_matches_oracle(name):
         want_c += oc
     assert rel_l2(gw, want_w) <= TOL_GRAD, rel_l2(gw, want_w)
     assert abs(gc - want_c) <= 1e-3 * abs(want_c), (gc, want_c)
+
+
+# Grids with the axial spacing of the batched differentiable PWI workload (512 rows over
+# 5-30 mm at 50 MHz: dz = 1.6 samples) and fewer elements, angles and frames, so the FP64
+# oracle stays cheap.  On these grids both the forward and the reverse call take their
+# tiled kernels (asserted through wf_das_plan), the reverse one with the reciprocal STAI
+# pairing where every element fires in order.
+FINE_CASES = {
+    "pwi_fine": dict(mode="pwi", seed=80, n_elements=64, n_tx=3, n_samples=2048, nz=512, nx=256,
+                     z_range=(5e-3, 30e-3), batch=2, t_start=1.0),
+    "stai_fine_reciprocal": dict(mode="stai", seed=81, n_elements=32, n_tx=32, n_samples=1024,
+                                 nz=256, nx=128, z_range=(5e-3, 17.5e-3), t_start=5e-7),
+}
+
+
+@pytest.mark.parametrize("name", sorted(FINE_CASES))
+@pytest.mark.parametrize("tile", [None, "4,4", "4,2"])
+def test_tiled_backward_on_fine_grid_matches_oracle(name, tile, monkeypatch):
+    kw = dict(FINE_CASES[name])
+    case = configs.random_case(kw.pop("mode"), kw.pop("seed"), elem_weight=True, fs=50e6, **kw)
+    if tile is not None:
+        monkeypatch.setenv("WF_DAS_TILE", tile)
+    wf.reload_tuning()
+    pr, gr = _gpu_probe(case, case.elem_weight)
+    scan = _scan(case)
+    fwd_plan = wf.das_plan(pr, gr, case.mode, n_tx=case.n_tx, n_samples=case.n_samples,
+                           batch=case.batch, **scan)
+    bwd_plan = wf.das_plan(pr, gr, case.mode, n_tx=case.n_tx, n_samples=case.n_samples,
+                           batch=case.batch, reverse=True, **scan)
+    assert fwd_plan["tiled"] == 1 and bwd_plan["tiled"] == 1, (fwd_plan, bwd_plan)
+    assert fwd_plan["tile_rows"] == {None: 32, "4,4": 32, "4,2": 16}[tile]
+    assert bwd_plan["tile_rows"] == 16          # the reverse kernel's 32 x 16 tiles
+    assert bwd_plan["reciprocal"] == (1 if case.mode == "stai" else 0)
+    rf = torch.from_numpy(case.rf).cuda()
+    # forward parity on the same grid (the image the gradient belongs to)
+    got = (wf.das_stai if case.mode == "stai" else wf.das_pwi)(rf, pr, gr, **scan).cpu().numpy()
+    for b in range(case.batch):
+        want = oracle.das(case, frame=b, threads=THREADS)
+        assert rel_l2(got[b], want) <= 1e-4, (b, rel_l2(got[b], want))
+    # RF and weight gradients: a random cotangent, element by element
+    rng = np.random.default_rng(2)
+    y = rng.standard_normal((case.batch, case.nz, case.nx))
+    grf, gw, _ = wf.das_backward(rf, torch.from_numpy(y).float().cuda(), pr, gr, case.mode,
+                                 need_c=False, **scan)
+    grf, gw = grf.cpu().numpy(), gw.cpu().numpy()
+    want_w = np.zeros(case.n_elements)
+    for b in range(case.batch):
+        orf, ow, _ = oracle.das_backward_case(case, y[b].astype(np.float32).astype(np.float64),
+                                              frame=b, threads=THREADS, need=("rf", "g"))
+        assert rel_l2(grf[b], orf) <= TOL_GRAD, (b, rel_l2(grf[b], orf))
+        want_w += ow
+    assert rel_l2(gw, want_w) <= TOL_GRAD, rel_l2(gw, want_w)
+    # Sound speed.  ds/dc multiplies the slope of the interpolation segment the delay falls
+    # on, which jumps at every sample, so a term whose FP32 and FP64 delays straddle a sample
+    # (both well inside the delay budget) contributes a different slope.  Under a random
+    # cotangent dL/dc is a small remainder of a cancelling sum, and shifting every oracle
+    # delay by 5e-5 samples moves it by several percent.  The cotangent here is the oracle's
+    # own derivative image y = db/dc (FP64 central difference), which makes dL/dc = <db/dc,
+    # db/dc> a sum of squares: the same shift moves it by about 1e-4 of itself.
+    h = 1e-4 * case.c
+    yc = np.stack([(oracle.das(dc_replace(case, c=case.c + h), frame=b, threads=THREADS) -
+                    oracle.das(dc_replace(case, c=case.c - h), frame=b, threads=THREADS)) / (2 * h)
+                   for b in range(case.batch)])
+    yc = (yc / np.abs(yc).max()).astype(np.float32)
+    _, _, gc = wf.das_backward(rf, torch.from_numpy(yc).cuda(), pr, gr, case.mode,
+                               need_rf=False, need_weight=False, **scan)
+    want_c = sum(oracle.das_backward_case(case, yc[b].astype(np.float64), frame=b,
+                                          threads=THREADS, need=("c",))[2]
+                 for b in range(case.batch))
+    assert abs(gc.item() - want_c) <= 1e-3 * abs(want_c), (gc.item(), want_c)
 
 
 @pytest.mark.parametrize("name", ["stai_sym", "pwi"])
