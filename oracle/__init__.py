@@ -107,6 +107,9 @@ def _load():
             lib.or_iq_demod.argtypes = [dp, C.c_int32, C.c_double, C.c_double, dp, C.c_int32,
                                         C.c_int32, dp]
             lib.or_iq_demod.restype = None
+            lib.or_das_iq.argtypes = [P, G, C.c_int32, C.c_int32, ip, dp, dp, C.c_int32, C.c_int32,
+                                      C.c_int32, C.c_double, dp, C.c_int32, C.c_int32, dp]
+            lib.or_das_iq.restype = C.c_int
             _lib = lib
     return _lib
 
@@ -442,6 +445,46 @@ def iq_demod(x, f0, fs, taps, decim: int = 1) -> np.ndarray:
         lib.or_iq_demod(_dp(row), ns, float(f0), float(fs), _dp(h), len(h), int(decim), _dp(o))
         out[i] = o[0::2] + 1j * o[1::2]
     return out.reshape(xx.shape[:-1] + (n_out,))
+
+
+def das_iq(iq, probe: Probe, grid: Grid, *, mode: str, decim: int, f0: float, tx_elem=None,
+           t_start=0.0, angles=None, t_starts=None, rows=None, threads: int = 1) -> np.ndarray:
+    """Delay-and-sum of complex baseband traces iq [n_tx][n_rx][M] (the output of
+    ``iq_demod`` with decimation ``decim``) -> complex image [nz][nx] (or_das_iq)."""
+    lib = _load()
+    z = np.asarray(iq)
+    n_tx, n_rx, m = z.shape
+    buf = np.empty((n_tx, n_rx, m, 2))
+    buf[..., 0] = z.real
+    buf[..., 1] = np.imag(z) if np.iscomplexobj(z) else 0.0
+    buf = np.ascontiguousarray(buf)
+    ps, _w = probe._c()
+    g = grid._c()
+    if mode == "stai":
+        mcode, ang = 0, None
+        tx = None if tx_elem is None else np.ascontiguousarray(tx_elem, dtype=np.int32)
+        ts = _f64([float(t_start or 0.0)])
+    else:
+        mcode, tx = 1, None
+        ang = _f64(angles)
+        ts = _f64(np.zeros(n_tx) if t_starts is None else t_starts)
+    txp = tx.ctypes.data_as(C.POINTER(C.c_int32)) if tx is not None else C.POINTER(C.c_int32)()
+    angp = _dp(ang) if ang is not None else C.POINTER(C.c_double)()
+    out = np.zeros((grid.nz, grid.nx, 2))
+
+    def run(ab):
+        rc = lib.or_das_iq(C.byref(ps), C.byref(g), mcode, n_tx, txp, angp, _dp(ts), n_rx, m,
+                           int(decim), float(f0), _dp(buf), ab[0], ab[1], _dp(out))
+        if rc:
+            raise ValueError("oracle das_iq: n_rx must equal n_elements and decim >= 1")
+
+    chunks = _row_chunks(grid.nz, rows, threads)
+    if len(chunks) == 1:
+        run(chunks[0])
+    else:
+        with ThreadPoolExecutor(len(chunks)) as ex:
+            list(ex.map(run, chunks))
+    return out[..., 0] + 1j * out[..., 1]
 
 
 def das(case, frame: int = 0, threads: int = 1, rows=None) -> np.ndarray:

@@ -505,3 +505,62 @@ void or_iq_demod(const double* x, int32_t ns, double f0, double fs, const double
         iq[2 * m + 1] = im;
     }
 }
+
+/*
+ * Delay-and-sum of complex baseband (IQ) traces, STAI (mode 0) or PWI (mode 1):
+ * beamforming after IQ demodulation (pre-processing variant of Sec. II-B).
+ * iq[t][r][m] = (re, im) holds the output of or_iq_demod with decimation D,
+ * baseband sample m taken at RF sample index m D.  For every pixel and every
+ * (t, r) with non-zero weights: the delay s in RF samples (or_delay_stai /
+ * or_delay_pwi), its baseband position u = s / D, linear interpolation of I
+ * and Q at u with both recorded neighbours required (0 <= floor(u) and
+ * floor(u) + 1 <= M - 1, else the term is 0), and the remodulation phase
+ * exp(+2 pi i f0 s / fs) that undoes the mixing at that sample:
+ *   B(p) = sum_t w_t sum_r w_r lerp(iq[t][r], s / D) exp(2 pi i f0 s / fs)
+ * (w_t = 1 for PWI; weights as or_das_stai / or_das_pwi).  Writes rows
+ * [row_begin, row_end) of out[nz][nx][2].
+ */
+int or_das_iq(const or_probe* p, const or_grid* g, int32_t mode, int32_t n_tx,
+              const int32_t* tx_elem, const double* angles, const double* t_start, int32_t n_rx,
+              int32_t m_samples, int32_t decim, double f0, const double* iq, int32_t row_begin,
+              int32_t row_end, double* out)
+{
+    if (n_rx != p->n_elements || decim < 1) return 1;
+    for (int32_t iz = row_begin; iz < row_end; ++iz) {
+        double z = or_pixel_z(g, iz);
+        for (int32_t ix = 0; ix < g->nx; ++ix) {
+            double x = or_pixel_x(g, ix);
+            double acc_re = 0.0, acc_im = 0.0;
+            for (int32_t t = 0; t < n_tx; ++t) {
+                int32_t et = mode == 0 ? (tx_elem ? tx_elem[t] : t) : -1;
+                double t0 = t_start ? t_start[mode == 0 ? 0 : t] : 0.0;
+                double wt = mode == 0 ? or_apod(p, x, z, et) : 1.0;
+                if (wt == 0.0) continue;
+                double in_re = 0.0, in_im = 0.0;
+                for (int32_t r = 0; r < n_rx; ++r) {
+                    double wr = or_apod(p, x, z, r);
+                    if (wr == 0.0) continue;
+                    double s = mode == 0 ? or_delay_stai(p, x, z, et, r, t0)
+                                         : or_delay_pwi(p, x, z, angles[t], r, t0);
+                    double u = s / (double)decim;
+                    double fu = floor(u);
+                    if (!(fu >= 0.0) || !(fu + 1.0 <= (double)(m_samples - 1))) continue;
+                    int64_t i = (int64_t)fu;
+                    double f = u - fu;
+                    const double* tr = iq + ((size_t)t * n_rx + r) * (size_t)m_samples * 2;
+                    double vr = (1.0 - f) * tr[2 * i] + f * tr[2 * i + 2];
+                    double vi = (1.0 - f) * tr[2 * i + 1] + f * tr[2 * i + 3];
+                    double ph = 2.0 * M_PI * f0 * s / p->fs;
+                    double c = cos(ph), sn = sin(ph);
+                    in_re += wr * (vr * c - vi * sn);
+                    in_im += wr * (vr * sn + vi * c);
+                }
+                acc_re += wt * in_re;
+                acc_im += wt * in_im;
+            }
+            out[2 * ((size_t)iz * g->nx + ix)] = acc_re;
+            out[2 * ((size_t)iz * g->nx + ix) + 1] = acc_im;
+        }
+    }
+    return 0;
+}

@@ -14,6 +14,7 @@ import pytest
 import oracle
 import test_oracle_fir_pins as fir_pins
 import test_oracle_grad_pins as grad_pins
+import test_oracle_iq_pins as iq_pins
 import test_oracle_pins as pins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "oracle.c")
@@ -76,10 +77,29 @@ MUTANTS = {
                              ["test_iq_demod_at_zero_frequency_is_the_fir", "test_iq_demod_of_a_tone_at_f0"]),
     "window_width": ("double half_width = 0.5 * z / p->f_number;", "double half_width = z / p->f_number;",
                      ["test_window_is_apod_without_weight", "test_adjoint_identity"]),
+    # delay-and-sum of IQ data
+    "iq_remod_sign": ("double c = cos(ph), sn = sin(ph);", "double c = cos(ph), sn = -sin(ph);",
+                      ["test_iq_das_single_element_phase_by_hand",
+                       "test_iq_das_envelope_matches_rf_envelope"]),
+    "iq_decimation_ignored": ("double u = s / (double)decim;", "double u = s;",
+                              ["test_iq_das_single_element_phase_by_hand",
+                               "test_iq_das_focuses_point_target"]),
+    "iq_imag_dropped": ("double vi = (1.0 - f) * tr[2 * i + 1] + f * tr[2 * i + 3];", "double vi = 0.0;",
+                        ["test_iq_das_single_element_phase_by_hand",
+                         "test_iq_das_envelope_matches_rf_envelope"]),
+    "iq_phase_at_baseband_index": ("double ph = 2.0 * M_PI * f0 * s / p->fs;",
+                                   "double ph = 2.0 * M_PI * f0 * u / p->fs;",
+                                   ["test_iq_das_single_element_phase_by_hand",
+                                    "test_iq_das_envelope_matches_rf_envelope"]),
+    "iq_rx_weight_dropped": ("in_re += wr * (vr * c - vi * sn);", "in_re += (vr * c - vi * sn);",
+                             ["test_iq_das_reduces_to_rf_das"]),
 }
 
 
 def _call(name, golden):
+    if hasattr(iq_pins, name):
+        getattr(iq_pins, name)()       # every mode and decimation of the pin
+        return
     if hasattr(fir_pins, name):
         fn = getattr(fir_pins, name)
         if "n_taps" in fn.__code__.co_varnames[: fn.__code__.co_argcount]:
