@@ -353,6 +353,55 @@ wf_status wf_iq_demod(const void* rf, wf_dtype dtype, float rf_scale, int64_t n_
 wf_status wf_fir_bandpass(double f_lo, double f_hi, double fs, int32_t n_taps, float* taps_out);
 
 /*
+ * Delay-and-sum of complex baseband (IQ) traces: beamforming after
+ * wf_iq_demod, the pre-processing variant of Sec. II-B's operators (FIR
+ * filtering before the beamformer).  iq holds the demodulator's output with
+ * decimation D: baseband sample m of a trace is the complex value at RF sample
+ * index m D.  For every pixel p:
+ *
+ *   B(p) = sum_t w_t sum_r w_r lerp(iq[t][r], s / D) exp(2 pi i f0 s / fs)
+ *
+ * with s(p, t, r) the delay in RF samples of wf_das_stai (STAI, w_t as there)
+ * or wf_das_pwi (PWI, w_t = 1), the same apodization, and lerp the linear
+ * interpolation of I and Q with both recorded neighbours required (0 <=
+ * floor(s / D) and floor(s / D) + 1 <= m_samples - 1, else the term is 0).
+ * The phase undoes the demodulator's mixing at the interpolated sample, so for
+ * taps of unit DC gain |B| is about half the envelope of the RF-domain image
+ * (wf_iq_envelope takes |B|).  Accumulation in FP32; the per-stage phase
+ * reduction in double-float, so no FP64 runs on the GPU.
+ *
+ *  n_rx         must equal probe->n_elements
+ *  m_samples    baseband samples per trace, 2..WF_MAX_SAMPLES
+ *  decim        D, 1..64 (wf_iq_demod's decimation)
+ *  f0           mixing frequency of wf_iq_demod, Hz (finite)
+ *  t_start      STAI: time of RF sample 0 (s); PWI: host [n_angles] or NULL = 0
+ *  iq           device float [batch][n_tx][n_rx][m_samples][2] (re, im), 8-byte aligned
+ *  out          device float [batch][nz][nx][2], the complex image B
+ *  ws, ws_bytes device workspace of at least wf_das_iq_workspace_bytes() bytes
+ * Grids so coarse that a pixel tile's staging window exceeds the tiled
+ * kernel's limit return WF_ERR_UNSUPPORTED (there is no per-pixel path).
+ */
+size_t wf_das_iq_workspace_bytes(const wf_probe* probe, const wf_grid* grid, int32_t mode,
+                                 int32_t batch, int32_t n_tx, int32_t m_samples, int32_t decim);
+wf_status wf_das_stai_iq(const wf_probe* probe, const wf_grid* grid, int32_t batch, int32_t n_tx,
+                         const int32_t* tx_elem, int32_t n_rx, int32_t m_samples, int32_t decim,
+                         double f0, double t_start, const float* iq, float* out, void* ws,
+                         size_t ws_bytes, wf_stream stream);
+wf_status wf_das_pwi_iq(const wf_probe* probe, const wf_grid* grid, int32_t batch,
+                        int32_t n_angles, const double* angles_rad, const double* t_start,
+                        int32_t n_rx, int32_t m_samples, int32_t decim, double f0, const float* iq,
+                        float* out, void* ws, size_t ws_bytes, wf_stream stream);
+
+/*
+ * Envelope of an IQ-beamformed image: env = |B| for every pixel of the complex
+ * image img [batch][nz][nx][2] (8-byte aligned), and, if frame_max is not
+ * NULL, each frame's largest non-NaN value (device float [batch]), ready for
+ * wf_logclip.  env is device float [batch][nz][nx].
+ */
+wf_status wf_iq_envelope(const float* img, int32_t batch, int32_t nz, int32_t nx, float* env,
+                         float* frame_max, wf_stream stream);
+
+/*
  * STAI delay-and-sum exactly as wf_das_stai, without a caller workspace.
  * (No counterpart in the paper: this entry point exists for callers that
  * cannot allocate device memory, such as a real-time acquisition loop whose
@@ -404,8 +453,8 @@ wf_status wf_fixed_scratch_check(wf_stream stream);
  * keys), so a repeated call with the same geometry only sets its pointers and
  * launches.  Element weights are device data, read at run time, and not part
  * of a plan.  The optional tuning switches (environment variables
- * WF_DAS_NO_SYM, WF_DAS_NO_TMA, WF_DAS_TILE, WF_DAS_GROUPS, WF_DAS_BUDGET,
- * WF_DAS_RING, WF_CHECK_BOUNDS) are read on the first DAS call;
+ * WF_DAS_NO_SYM, WF_DAS_NO_TMA, WF_DAS_NO_TMAP, WF_DAS_TILE, WF_DAS_GROUPS,
+ * WF_DAS_BUDGET, WF_DAS_RING, WF_CHECK_BOUNDS) are read on the first DAS call;
  * wf_das_reload_tuning re-reads them and drops every cached plan.  Host only;
  * safe to call from any thread between calls.
  */

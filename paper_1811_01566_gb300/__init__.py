@@ -26,7 +26,7 @@ __all__ = ["Probe", "Grid", "WfError", "HANN", "RECT", "NONE", "das_stai", "das_
            "das_workspace_bytes", "das_delays", "das_backward", "das", "envelope", "logclip",
            "envelope_backward", "logclip_backward", "bmode", "bmode_diff", "fir", "iq_demod",
            "fir_bandpass", "workspace_check", "rf_boxes", "copy_rf_boxes", "library_path",
-           "version", "reload_tuning", "das_plan"]
+           "version", "reload_tuning", "das_plan", "das_iq", "iq_envelope"]
 
 HANN, RECT, NONE = 0, 1, 2
 _DTYPES = {torch.float32: 0, torch.float16: 1, torch.int16: 2}
@@ -116,6 +116,16 @@ def _load():
             lib.wf_das_rf_boxes.restype = C.c_int
             lib.wf_copy_rf_boxes.argtypes = [vp, vp, i32, i32, i32, i32, vp, i32, vp]
             lib.wf_copy_rf_boxes.restype = C.c_int
+            lib.wf_das_iq_workspace_bytes.argtypes = [P, G, i32, i32, i32, i32, i32]
+            lib.wf_das_iq_workspace_bytes.restype = sz
+            lib.wf_das_stai_iq.argtypes = [P, G, i32, i32, vp, i32, i32, i32, f64, f64, vp, vp, vp,
+                                           sz, vp]
+            lib.wf_das_stai_iq.restype = C.c_int
+            lib.wf_das_pwi_iq.argtypes = [P, G, i32, i32, vp, vp, i32, i32, i32, f64, vp, vp, vp, sz,
+                                          vp]
+            lib.wf_das_pwi_iq.restype = C.c_int
+            lib.wf_iq_envelope.argtypes = [vp, i32, i32, i32, vp, vp, vp]
+            lib.wf_iq_envelope.restype = C.c_int
             lib.wf_das_plan.argtypes = [P, G, i32, i32, i32, i32, vp, vp, vp, i32, i32,
                                         C.POINTER(_WfPlanInfo)]
             lib.wf_das_plan.restype = C.c_int
@@ -231,6 +241,59 @@ def das_plan(probe: Probe, grid: Grid, mode: str, *, n_tx: int, n_samples: int,
                                int(bool(reverse)), int(batch), int(n_tx), tx, ang, ts, int(n_samples),
                                _DTYPES[dtype], C.byref(info)), "wf_das_plan")
     return {n: getattr(info, n) for n, _ in _WfPlanInfo._fields_}
+
+
+def das_iq(iq: torch.Tensor, probe: Probe, grid: Grid, mode: str, *, decim: int, f0: float,
+           tx_elem=None, t_start=None, angles=None, out: torch.Tensor | None = None,
+           workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Delay-and-sum of IQ data (the output of ``iq_demod``: complex64 [batch, n_tx, n_rx, m]
+    or [n_tx, n_rx, m]) -> complex64 image [batch, nz, nx]; see wf_das_stai_iq / wf_das_pwi_iq."""
+    if iq.dim() == 3:
+        iq = iq.unsqueeze(0)
+    if not (iq.is_cuda and iq.dtype == torch.complex64 and iq.is_contiguous() and iq.dim() == 4):
+        raise ValueError("iq must be a contiguous CUDA complex64 [batch, n_tx, n_rx, m] tensor")
+    b, n_tx, n_rx, m = iq.shape
+    lib = _load()
+    mcode = {"stai": 0, "pwi": 1}[mode]
+    need = lib.wf_das_iq_workspace_bytes(C.byref(probe._c()), C.byref(grid._c()), mcode, b, n_tx, m,
+                                         int(decim))
+    if need == 0:
+        raise WfError(2, "wf_das_iq_workspace_bytes")
+    if workspace is None:
+        workspace = torch.empty(need, device=iq.device, dtype=torch.uint8)
+    if out is None:
+        out = torch.empty(b, grid.nz, grid.nx, device=iq.device, dtype=torch.complex64)
+    ws_n = workspace.numel() * workspace.element_size()
+    if mode == "stai":
+        tx = None if tx_elem is None else (C.c_int32 * n_tx)(*[int(v) for v in tx_elem])
+        st = lib.wf_das_stai_iq(C.byref(probe._c()), C.byref(grid._c()), b, n_tx, tx, n_rx, m,
+                                int(decim), float(f0), float(t_start or 0.0), iq.data_ptr(),
+                                out.data_ptr(), workspace.data_ptr(), ws_n, _stream(stream))
+    else:
+        ang = _f64_array(angles, n_tx)
+        ts = None if t_start is None else _f64_array(t_start, n_tx)
+        st = lib.wf_das_pwi_iq(C.byref(probe._c()), C.byref(grid._c()), b, n_tx, ang, ts, n_rx, m,
+                               int(decim), float(f0), iq.data_ptr(), out.data_ptr(),
+                               workspace.data_ptr(), ws_n, _stream(stream))
+    _check(st, "wf_das_stai_iq" if mode == "stai" else "wf_das_pwi_iq")
+    return out
+
+
+def iq_envelope(img: torch.Tensor, *, out: torch.Tensor | None = None, with_max: bool = True,
+                frame_max: torch.Tensor | None = None, stream=None):
+    """|B| of a complex64 image [batch, nz, nx] -> (env float32, frame_max or None)."""
+    if img.dim() == 2:
+        img = img.unsqueeze(0)
+    if not (img.is_cuda and img.dtype == torch.complex64 and img.is_contiguous()):
+        raise ValueError("img must be a contiguous CUDA complex64 tensor")
+    b, nz, nx = img.shape
+    out = torch.empty(b, nz, nx, device=img.device, dtype=torch.float32) if out is None else out
+    if with_max and frame_max is None:
+        frame_max = torch.empty(b, device=img.device, dtype=torch.float32)
+    fm = frame_max.data_ptr() if (with_max and frame_max is not None) else None
+    _check(_load().wf_iq_envelope(img.data_ptr(), b, nz, nx, out.data_ptr(), fm, _stream(stream)),
+           "wf_iq_envelope")
+    return out, (frame_max if with_max else None)
 
 
 def reload_tuning() -> None:

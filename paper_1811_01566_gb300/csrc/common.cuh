@@ -1,6 +1,7 @@
 // Internal helpers shared by the CUDA translation units of libwf (not part of the ABI).
 #pragma once
 
+#include <cuda.h>            // CUtensorMap (the descriptor type only; no driver API is linked)
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 #include <stdint.h>

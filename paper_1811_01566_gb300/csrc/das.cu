@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <cstddef>
 #include <cstring>
 #include <list>
 #include <memory>
@@ -94,12 +95,13 @@ namespace {
 
 bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
 
-// Tuning switches from the environment (WF_DAS_NO_SYM, WF_DAS_NO_TMA, WF_DAS_TILE,
+// Tuning switches from the environment (WF_DAS_NO_SYM, WF_DAS_NO_TMA, WF_DAS_NO_TMAP, WF_DAS_TILE,
 // WF_DAS_GROUPS, WF_DAS_BUDGET, WF_DAS_RING, WF_CHECK_BOUNDS), read on the first DAS
 // call and again only on wf_das_reload_tuning(); `gen` counts the reloads, so plans
 // cached under older switches are never reused.
 struct Tuning {
     bool no_sym = false, no_tma = false, check_bounds = false;
+    bool no_tmap = false;         // per-trace bulk copies instead of tensor-map boxes
     int tile_w = 0, tile_p = 0;   // 0: no tile override
     int groups = 0;               // > 0: uniform groups instead of the schedule
     int budget = 0;               // > 0: CTAs per frame of the schedule
@@ -121,6 +123,7 @@ void read_tuning_locked() {
     t.gen = g_tuning.gen + 1;
     t.no_sym = env_flag("WF_DAS_NO_SYM");
     t.no_tma = env_flag("WF_DAS_NO_TMA");
+    t.no_tmap = env_flag("WF_DAS_NO_TMAP");
     t.check_bounds = env_flag("WF_CHECK_BOUNDS");
     if (const char* v = std::getenv("WF_DAS_TILE"))
         if (std::sscanf(v, "%d,%d", &t.tile_w, &t.tile_p) != 2) t.tile_w = t.tile_p = 0;
@@ -426,6 +429,59 @@ double fill_tx(DasArgs& a, const wf_probe* probe, int mode, int n_tx, const int3
                const double* angles, const double* t_start, bool per_tx_start);
 
 // ---------------------------------------------------------------------------
+// TMA descriptors of the RF array.  cuTensorMapEncodeTiled is reached through the
+// runtime's driver entry point, so the library links no driver API.
+// ---------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+// Descriptors of rf as [frames * n_tx][E][ns / 8][8] for boxes of (W + 8) samples of 8
+// receive rows (tm_rows) and of 8 transmit rows (tm_cols); false when they cannot be made
+// (the call then takes the per-trace bulk copies).  Requires ns % 8 == 0 and a 16-byte
+// aligned rf: every stride is then a multiple of 16 bytes and every box row 16-byte long.
+bool encode_rf_maps(DasArgs& A, const void* rf, wf_dtype dt, long long frames_tx, int E, int ns,
+                    int W, bool sym) {
+    const EncodeTiledFn fn = encode_tiled();
+    if (!fn || ns % 8 != 0 || ((uintptr_t)rf & 15u) || (W + 8) / 8 > 256) return false;
+    const cuuint64_t eb = dt == WF_F32 ? 4 : 2;
+    const CUtensorMapDataType ty = dt == WF_F32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : dt == WF_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                  : CU_TENSOR_MAP_DATA_TYPE_UINT16;
+    const cuuint64_t dims[4] = {8, (cuuint64_t)ns / 8, (cuuint64_t)E, (cuuint64_t)frames_tx};
+    const cuuint64_t strides[3] = {8 * eb, (cuuint64_t)ns * eb, (cuuint64_t)E * ns * eb};
+    const cuuint32_t g = (cuuint32_t)(W + 8) / 8;
+    const cuuint32_t box_rows[4] = {8, g, (cuuint32_t)kC, 1};
+    const cuuint32_t box_cols[4] = {8, g, 1, (cuuint32_t)kC};
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    void* base = const_cast<void*>(rf);
+    if (fn(&A.tm_rows, ty, 4, base, dims, strides, box_rows, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    if (sym && fn(&A.tm_cols, ty, 4, base, dims, strides, box_cols, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    return true;
+}
+
+// ---------------------------------------------------------------------------
 // Plan cache.  A DAS call's plan (tile configuration, staging, workspace layout),
 // its transmit table and its CTA schedule depend only on the probe, grid, scan,
 // batch, RF shape and type and the tuning switches, so they are built once per
@@ -544,6 +600,9 @@ wf_status das_run(int mode, const wf_probe* probe, const wf_grid* grid, int32_t 
     A.tile_info = reinterpret_cast<unsigned*>(static_cast<char*>(ws) + kWsHeaderBytes);
     A.part = reinterpret_cast<float*>(static_cast<char*>(ws) + kWsHeaderBytes + P.info_bytes);
     A.out = out;
+    A.use_tmap = P.tiled && P.tma && !tuning().no_tmap &&
+                 encode_rf_maps(A, rf, dtype, (long long)batch * n_tx, probe->n_elements, n_samples,
+                                P.W, P.sym);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if ((s = cuda_status(cudaMemsetAsync(ws, 0, kWsHeaderBytes + P.info_bytes, st))) != WF_OK) return s;
     return mode == 0 ? dispatch<0>(A, P, batch, dtype, st) : dispatch<1>(A, P, batch, dtype, st);
@@ -916,6 +975,119 @@ extern "C" wf_status wf_das_plan(const wf_probe* probe, const wf_grid* grid, int
     info->smem_bytes = P.tiled ? (int32_t)P.smem : 0;
     info->workspace_bytes = (int64_t)P.ws_bytes;
     return WF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Delay-and-sum of IQ data: the RF path's geometry and tiles in baseband samples
+// (fs / D), kernels in das_iq.cu.
+// ---------------------------------------------------------------------------
+namespace wf {
+namespace {
+
+wf_status das_iq_prepare(int mode, const wf_probe* probe, const wf_grid* grid, int32_t batch,
+                         int32_t n_tx, const int32_t* tx_elem, const double* angles,
+                         const double* t_start, int32_t n_rx, int32_t m_samples, int32_t decim,
+                         double f0, DasArgs& A, size_t& ws_need) {
+    wf_status s = check_probe_grid(probe, grid);
+    if (s != WF_OK) return s;
+    if (batch < 1 || batch > 65535 || n_tx < 1 || n_tx > WF_MAX_TX) return WF_ERR_INVALID_ARG;
+    if (n_rx != probe->n_elements || m_samples < 2 || m_samples > WF_MAX_SAMPLES) return WF_ERR_INVALID_ARG;
+    if (decim < 1 || decim > 64 || !std::isfinite(f0)) return WF_ERR_INVALID_ARG;
+    if (mode == 1 && !angles) return WF_ERR_INVALID_ARG;
+    wf_probe pb = *probe;
+    pb.fs = probe->fs / decim;                       // baseband samples
+    std::memset(&A, 0, offsetof(DasArgs, tx));
+    const double extra = fill_tx(A, &pb, mode, n_tx, tx_elem, angles, t_start, mode == 1);
+    if (extra < 0.0) return WF_ERR_INVALID_ARG;
+    if (2.0 * max_delay(&pb, grid) + extra >= 4194304.0) return WF_ERR_UNSUPPORTED;
+    GeomD D;
+    make_geom(&pb, grid, A.g, D);
+    make_geom(&pb, grid, A.g, A.gd);
+    const Plan P = plan_for(mode, Cfg{4, 2}, D, &pb, grid, batch, n_tx, m_samples, 8, false);
+    if (!P.tiled || iq_smem_bytes(P.W, probe->n_elements) > kMaxTiledSmem) return WF_ERR_UNSUPPORTED;
+    A.n_tx = n_tx;
+    A.ns = m_samples;
+    A.tiles_x = P.tiles_x;
+    A.tiles_z = P.tiles_z;
+    A.n_groups = std::max(1, std::min(kMaxGroups, P.n_groups));
+    A.n_items = P.tiles_x * P.tiles_z * A.n_groups;
+    A.W = P.W;
+    A.sym = 0;
+    A.use_table = 0;
+    A.use_tmap = 0;
+    A.frame_elems = (long long)n_tx * probe->n_elements * m_samples;
+    A.iq_k = df_from_double(f0 * decim / probe->fs);
+    ws_need = kWsHeaderBytes + (size_t)batch * A.n_items * kThreads * 2 * 2 * sizeof(float);
+    return WF_OK;
+}
+
+wf_status das_iq_run(int mode, const wf_probe* probe, const wf_grid* grid, int32_t batch,
+                     int32_t n_tx, const int32_t* tx_elem, const double* angles,
+                     const double* t_start, int32_t n_rx, int32_t m_samples, int32_t decim,
+                     double f0, const float* iq, float* out, void* ws, size_t ws_bytes,
+                     wf_stream stream) {
+    thread_local DasArgs A;
+    size_t need = 0;
+    wf_status s = das_iq_prepare(mode, probe, grid, batch, n_tx, tx_elem, angles, t_start, n_rx,
+                                 m_samples, decim, f0, A, need);
+    if (s != WF_OK) return s;
+    if (!iq || !out || ((uintptr_t)iq & 7u) || ((uintptr_t)out & 7u)) return WF_ERR_INVALID_ARG;
+    if (!ws || ((uintptr_t)ws & 15u) || ws_bytes < need) return WF_ERR_WORKSPACE;
+    A.g.elem_weight = probe->elem_weight;
+    A.rf = iq;
+    A.rf_scale = 1.0f;
+    A.hdr = static_cast<WsHeader*>(ws);
+    A.part = reinterpret_cast<float*>(static_cast<char*>(ws) + kWsHeaderBytes);
+    A.out = out;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if ((s = cuda_status(cudaMemsetAsync(ws, 0, kWsHeaderBytes, st))) != WF_OK) return s;
+    return mode == 0 ? launch_das_iq<0>(A, batch, out, st) : launch_das_iq<1>(A, batch, out, st);
+}
+
+}  // namespace
+}  // namespace wf
+
+extern "C" size_t wf_das_iq_workspace_bytes(const wf_probe* probe, const wf_grid* grid, int32_t mode,
+                                            int32_t batch, int32_t n_tx, int32_t m_samples,
+                                            int32_t decim) {
+    thread_local DasArgs A;
+    if ((mode != 0 && mode != 1) || n_tx < 1 || n_tx > WF_MAX_TX) return 0;
+    std::vector<double> ang(n_tx, 0.0);
+    const double t0 = 0.0;
+    size_t need = 0;
+    if (das_iq_prepare(mode, probe, grid, batch, n_tx, nullptr, ang.data(), &t0,
+                       probe ? probe->n_elements : 0, m_samples, decim, 0.0, A, need) != WF_OK)
+        return 0;
+    return need;
+}
+
+extern "C" wf_status wf_das_stai_iq(const wf_probe* probe, const wf_grid* grid, int32_t batch,
+                                    int32_t n_tx, const int32_t* tx_elem, int32_t n_rx,
+                                    int32_t m_samples, int32_t decim, double f0, double t_start,
+                                    const float* iq, float* out, void* ws, size_t ws_bytes,
+                                    wf_stream stream) {
+    if (!probe || !std::isfinite(t_start)) return WF_ERR_INVALID_ARG;
+    return das_iq_run(0, probe, grid, batch, n_tx, tx_elem, nullptr, &t_start, n_rx, m_samples,
+                      decim, f0, iq, out, ws, ws_bytes, stream);
+}
+
+extern "C" wf_status wf_das_pwi_iq(const wf_probe* probe, const wf_grid* grid, int32_t batch,
+                                   int32_t n_angles, const double* angles_rad, const double* t_start,
+                                   int32_t n_rx, int32_t m_samples, int32_t decim, double f0,
+                                   const float* iq, float* out, void* ws, size_t ws_bytes,
+                                   wf_stream stream) {
+    if (!probe || !angles_rad) return WF_ERR_INVALID_ARG;
+    return das_iq_run(1, probe, grid, batch, n_angles, nullptr, angles_rad, t_start, n_rx,
+                      m_samples, decim, f0, iq, out, ws, ws_bytes, stream);
+}
+
+extern "C" wf_status wf_iq_envelope(const float* img, int32_t batch, int32_t nz, int32_t nx,
+                                    float* env, float* frame_max, wf_stream stream) {
+    if (!img || !env || batch < 1 || nz < 1 || nx < 1 || ((uintptr_t)img & 7u) || ((uintptr_t)env & 3u))
+        return WF_ERR_INVALID_ARG;
+    if (frame_max && ((uintptr_t)frame_max & 3u)) return WF_ERR_INVALID_ARG;
+    return launch_iq_envelope(img, batch, (long long)nz * nx, env, frame_max,
+                              reinterpret_cast<cudaStream_t>(stream));
 }
 
 extern "C" wf_status wf_das_reload_tuning(void) {

@@ -65,6 +65,13 @@ struct GeomDF {
 };
 
 struct DasArgs {
+    // TMA descriptors of the RF array viewed as [frames * n_tx][E][ns / 8][8] (dimensions
+    // listed slowest first): boxes of 8 receive rows of one transmit (tm_rows) and of one
+    // receive column of 8 transmits (tm_cols, the mirrored rows of reciprocal STAI), each
+    // (W + 8) samples long.  Filled per call when use_tmap is set.
+    CUtensorMap tm_rows;
+    CUtensorMap tm_cols;
+    int use_tmap;
     Geom g;
     GeomDF gd;
     int n_tx, ns;
@@ -91,6 +98,8 @@ struct DasArgs {
     float* grad_w;                   // [E] or null
     float* grad_c;                   // [1] or null
     float neg_inv_c;                 // -1 / c (s per m/s of sound speed)
+    // IQ data (wf_das_stai_iq / wf_das_pwi_iq): remodulation rate, cycles per baseband sample
+    DF iq_k;
     TxInfo tx[WF_MAX_TX];
 };
 
@@ -332,6 +341,17 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsign
         "l"(src), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
 }
+// 4-D tensor copy (TMA) of one box of the descriptor at coordinates {c0, c1, c2, c3}
+// (fastest first) into shared memory, completion counted on the mbarrier.
+__device__ __forceinline__ void tensor_copy_4d(void* dst, const CUtensorMap* map, int c0, int c1,
+                                               int c2, int c3, unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3),
+        "r"(smem_u32(bar))
+        : "memory");
+}
 __device__ __forceinline__ void fence_async_shared() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -541,9 +561,10 @@ __host__ __device__ inline SmemLayout smem_layout(int W, int n_elements, bool db
     off += (size_t)kTableStages * sizeof(Stage);
     L.elems = off;
     off += (((size_t)n_elements * sizeof(Elem)) + 15) & ~(size_t)15;
+    off = (off + 127) & ~(size_t)127;   // tensor copies land on 128-byte boundaries
     L.raw = off;
     off += tma ? (size_t)ring * (sym ? 2 : 1) * kC * (W + 8) * rf_bytes : 0;
-    L.total = off;
+    L.total = off + 128;                 // slack: the kernel aligns the dynamic base itself
     return L;
 }
 
@@ -672,7 +693,9 @@ __global__ void __launch_bounds__(kThreads, 2) das_tiled_kernel(const __grid_con
     float2* buf0 = reinterpret_cast<float2*>(smem_raw + L.pairs);   // [DB+1][kC][W] pairs
     Stage* st = reinterpret_cast<Stage*>(smem_raw + L.table);        // ring of compacted stages
     Elem* el = reinterpret_cast<Elem*>(smem_raw + L.elems);         // [E range]
-    T* raw = reinterpret_cast<T*>(smem_raw + L.raw);                // [ring][kRawRows][W + 8]
+    // [ring][kRawRows][W + 8] raw samples, 128-byte aligned for the tensor copies
+    const unsigned raw_pad = (128u - (smem_u32(smem_raw) & 127u)) & 127u;   // L.total keeps 128 B slack
+    T* raw = reinterpret_cast<T*>(smem_raw + raw_pad + L.raw);
     __shared__ __align__(8) unsigned long long s_bar[kMaxRing];
     __shared__ int s_tlist[WF_MAX_TX];
     __shared__ int s_info[4];
@@ -761,6 +784,21 @@ __global__ void __launch_bounds__(kThreads, 2) das_tiled_kernel(const __grid_con
         const Stage si = st[qq & (kTableStages - 1)];
         unsigned long long* bar = &s_bar[qq % ring];
         const int t = tx_of(si.j());
+        if (a.use_tmap) {
+            // one box of 8 trace rows (and, reciprocal, one of the 8 mirrored rows) per stage;
+            // samples outside the record and rows outside the array arrive as zeros
+            if (lane == 0) {
+                T* slot = raw + (size_t)(qq % ring) * kRawRows * RW;
+                const int r0s = er.x + si.k() * kC, fr = b * a.n_tx;
+                const unsigned box = (unsigned)(kC * RW) * (unsigned)sizeof(T);
+                fence_async_shared();
+                mbar_arrive_expect(bar, SYM ? 2u * box : box);
+                tensor_copy_4d(slot, &a.tm_rows, 0, si.lo >> 3, r0s, fr + t, bar);
+                if (SYM) tensor_copy_4d(slot + kC * RW, &a.tm_cols, 0, si.lo >> 3, t, fr + r0s, bar);
+            }
+            __syncwarp();
+            return;
+        }
         const int rr0 = er.x + si.k() * kC, nrow = min(rr0 + kC - 1, er.y) - rr0 + 1;
         const int na = max(si.lo, 0), nb = min(si.lo + si.len + 8, a.ns);
         const int ca = SYM ? max(t - rr0, 0) : 0;        // first chunk row paired with t
@@ -1150,6 +1188,17 @@ wf_status launch_tiled_cfg(DasArgs& A, const Plan& P, int batch, cudaStream_t st
 template <int MODE>
 wf_status launch_das_backward(DasArgs& A, const Plan& P, int batch, bool need_rf, bool need_par,
                               cudaStream_t st);
+
+// Delay-and-sum of IQ data (das_iq.cu): shared-memory layout, launch (tiled kernel and
+// the group reduction into the complex image out [batch][nz][nx][2]) and |B| with frame maxima.
+struct IqSmem {
+    size_t pairs, rot, table, elems, total;
+};
+size_t iq_smem_bytes(int W, int n_elements);
+template <int MODE>
+wf_status launch_das_iq(DasArgs& A, int batch, float* out, cudaStream_t st);
+wf_status launch_iq_envelope(const float* img, int batch, long long n_frame, float* env, float* frame_max,
+                             cudaStream_t st);
 
 // Whether the reverse-mode launcher takes the tiled kernel for this plan (das_grad.cu).
 bool backward_is_tiled(const Plan& P, int n_elements, bool need_rf);

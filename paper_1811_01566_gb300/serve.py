@@ -64,25 +64,36 @@ class Result:
     db: object = None         # numpy [nz, nx] dB image
     latency: float = 0.0      # seconds, arrival -> completion seen
     error: str | None = None
+    cold: bool = False        # its shape had no device slot when it was admitted (slot created for it)
 
 
 @dataclass
 class _Slot:
     key: tuple
     bytes: int
-    handle: object            # executor state
-    busy: object = None       # Request in flight
+    handle: object            # executor state (None while the creator thread builds it)
+    busy: list | None = None  # Requests in flight (a batch of one shape)
     last_used: float = 0.0
+    pending: object = None    # Future of an asynchronous creation
+    fresh: bool = True        # created for the requests now waiting on it
 
 
 class Server:
-    """FIFO continuous-batching loop with per-shape slots and an HBM budget."""
+    """FIFO continuous-batching loop with per-shape slots and an HBM budget.
+
+    ``max_batch`` requests of one shape that are queued when a slot of that shape
+    frees up are launched together as one batch.  With ``async_create`` a new
+    slot is built on a creator thread (allocation, warm-up, graph capture) while
+    the loop keeps admitting and retiring requests of other shapes; the
+    requests of the new shape wait for it in their queue order.
+    """
 
     def __init__(self, executor, hbm_budget: int, max_slots_per_shape: int = 4,
-                 clock=time.perf_counter):
+                 clock=time.perf_counter, max_batch: int = 1, async_create: bool = False):
         self.ex = executor
         self.budget = int(hbm_budget)
         self.max_per_shape = max_slots_per_shape
+        self.max_batch = max(1, int(max_batch))
         self.clock = clock
         self.t0 = clock()
         self.queue: deque[Request] = deque()
@@ -90,6 +101,12 @@ class Server:
         self.used = 0
         self.results: OrderedDict[int, Result] = OrderedDict()
         self.cancelled: set[int] = set()
+        self.failed: dict = {}               # shape key -> creation error
+        self.evictions = 0
+        self._creator = None
+        if async_create:
+            from concurrent.futures import ThreadPoolExecutor
+            self._creator = ThreadPoolExecutor(1, thread_name_prefix="slot-creator")
 
     def now(self) -> float:
         return self.clock() - self.t0
@@ -108,19 +125,28 @@ class Server:
 
     # -- one pass of the loop -----------------------------------------------------
     def step(self) -> int:
-        """Retire finished work, then admit queued requests; returns requests launched."""
+        """Finish slot creations, retire finished work, then admit queued requests (batching
+        queued requests of a shape into a free slot of it); returns requests launched."""
+        self._poll_creations()
         self._retire()
         launched = 0
         blocked_keys = set()
         pending = deque()
-        while self.queue:
-            req = self.queue.popleft()
+        queue = list(self.queue)
+        taken = [False] * len(queue)
+        for i, req in enumerate(queue):
+            if taken[i]:
+                continue
             if req.rid in self.cancelled:
                 self.cancelled.discard(req.rid)
                 self.results[req.rid] = Result(req.rid, latency=self.now() - req.arrival,
                                                error="cancelled")
                 continue
             key = req.key()
+            if key in self.failed:
+                self.results[req.rid] = Result(req.rid, latency=self.now() - req.arrival,
+                                               error=self.failed[key])
+                continue
             if key in blocked_keys:          # FIFO within a shape
                 pending.append(req)
                 continue
@@ -133,33 +159,57 @@ class Server:
                 self.results[req.rid] = Result(req.rid, latency=self.now() - req.arrival,
                                                error=slot)
                 continue
+            batch = [req]
+            for j in range(i + 1, len(queue)):   # later queued requests of the same shape
+                if len(batch) >= self.max_batch:
+                    break
+                r = queue[j]
+                if not taken[j] and r.rid not in self.cancelled and r.key() == key:
+                    batch.append(r)
+                    taken[j] = True
             try:
-                self.ex.launch(slot.handle, req)
+                self.ex.launch(slot.handle, batch)
             except Exception as exc:         # a request the library rejects fails alone
-                self.results[req.rid] = Result(req.rid, latency=self.now() - req.arrival,
-                                               error=f"launch failed: {exc}")
+                for r in batch:
+                    self.results[r.rid] = Result(r.rid, latency=self.now() - r.arrival,
+                                                 error=f"launch failed: {exc}")
                 continue
-            slot.busy = req
+            slot.busy = batch
+            slot.cold_batch = slot.fresh
+            slot.fresh = False
             slot.last_used = self.now()
-            launched += 1
+            launched += len(batch)
         self.queue = pending
         return launched
 
+    def _poll_creations(self):
+        for s in list(self.slots):
+            if s.pending is None or not s.pending.done():
+                continue
+            fut, s.pending = s.pending, None
+            try:
+                s.handle = fut.result()
+            except Exception as exc:
+                self.failed[s.key] = f"rejected: {exc}"
+                self.slots.remove(s)
+                self.used -= s.bytes
+
     def _retire(self):
         for s in self.slots:
-            if s.busy is not None and self.ex.done(s.handle):
-                req = s.busy
-                self.results[req.rid] = Result(req.rid, db=self.ex.result(s.handle),
-                                               latency=self.now() - req.arrival)
+            if s.busy is not None and s.pending is None and self.ex.done(s.handle):
+                imgs = self.ex.result(s.handle)
+                for r, img in zip(s.busy, imgs):
+                    self.results[r.rid] = Result(r.rid, db=img, latency=self.now() - r.arrival,
+                                                 cold=getattr(s, "cold_batch", False))
                 s.busy = None
                 s.last_used = self.now()
 
     def _slot_for(self, req, key):
         same = [s for s in self.slots if s.key == key]
         for s in same:
-            if s.busy is None:
+            if s.busy is None and s.pending is None:
                 return s
-        if len(same) >= self.max_per_shape:
+        if len(same) >= self.max_per_shape or any(s.pending is not None for s in same):
             return None
         try:
             need = self.ex.footprint(req)
@@ -168,13 +218,20 @@ class Server:
         if need > self.budget:
             return f"rejected: needs {need} bytes of device memory, budget {self.budget}"
         while self.used + need > self.budget:
-            idle = [s for s in self.slots if s.busy is None]
+            idle = [s for s in self.slots if s.busy is None and s.pending is None]
             if not idle:
                 return None
             victim = min(idle, key=lambda s: s.last_used)
             self.ex.release(victim.handle)
             self.slots.remove(victim)
             self.used -= victim.bytes
+            self.evictions += 1
+        if self._creator is not None:        # built off the admission path; the request waits
+            slot = _Slot(key, need, None, last_used=self.now(),
+                         pending=self._creator.submit(self.ex.create, req))
+            self.slots.append(slot)
+            self.used += need
+            return None
         try:
             handle = self.ex.create(req)
         except Exception as exc:
@@ -186,7 +243,7 @@ class Server:
 
     # -- driving a schedule -------------------------------------------------------
     def idle(self) -> bool:
-        return not self.queue and all(s.busy is None for s in self.slots)
+        return not self.queue and all(s.busy is None and s.pending is None for s in self.slots)
 
     def run(self, requests, poll_sleep: float = 0.0) -> OrderedDict:
         """Feed requests at their arrival times (server clock) until all are answered."""
@@ -203,13 +260,22 @@ class Server:
 
     def close(self):
         for s in self.slots:
+            if s.pending is not None:
+                try:
+                    s.handle = s.pending.result()
+                except Exception:
+                    continue
             self.ex.release(s.handle)
         self.slots.clear()
         self.used = 0
+        if self._creator is not None:
+            self._creator.shutdown(wait=True)
 
 
-def latency_stats(results) -> dict:
-    lat = np.array([r.latency for r in results.values() if r.error is None])
+def latency_stats(results, cold: bool | None = None) -> dict:
+    """p50 / p99 latency of the answered requests (all, or only cold / warm ones)."""
+    lat = np.array([r.latency for r in results.values()
+                    if r.error is None and (cold is None or r.cold == cold)])
     if lat.size == 0:
         return {"p50_ms": None, "p99_ms": None, "n": 0}
     return {"p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
@@ -217,73 +283,93 @@ def latency_stats(results) -> dict:
 
 
 class CudaExecutor:
-    """Executor over libwf on one CUDA device: slots with streams and captured graphs."""
+    """Executor over libwf on one CUDA device: slots with streams and captured graphs.
 
-    def __init__(self, device=None, use_graphs: bool = True):
+    A slot holds buffers for up to ``max_batch`` requests of its shape and one
+    CUDA graph per batch size (DAS -> envelope -> log-clip of the first b frames),
+    captured when the slot is created.  Graphs are captured in thread-local mode,
+    so a creator thread can build a slot while other streams keep running.
+    """
+
+    def __init__(self, device=None, use_graphs: bool = True, max_batch: int = 1):
         import torch
 
         import paper_1811_01566_gb300 as wf
         self.torch, self.wf = torch, wf
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else device
         self.use_graphs = use_graphs
+        self.max_batch = max(1, int(max_batch))
 
     def footprint(self, req) -> int:
         wf = self.wf
         n_tx = req.rf_host.shape[1]
-        ws = wf.das_workspace_bytes(req.probe, req.grid, 1, n_tx)
+        b = self.max_batch
+        ws = wf.das_workspace_bytes(req.probe, req.grid, b, n_tx)
         img = req.grid.nz * req.grid.nx * 4
-        return int(req.rf_host.numel() * req.rf_host.element_size() + ws + 3 * img + 256)
+        rf = req.rf_host[0].numel() * req.rf_host.element_size()
+        return int(b * rf + ws + 3 * b * img + 256 * b)
 
-    def _pipeline(self, h, req):
+    def _pipeline(self, h, req, b):
         wf = self.wf
         das = wf.das_stai if req.mode == "stai" else wf.das_pwi
-        das(h["rf"], req.probe, req.grid, rf_scale=req.rf_scale, out=h["bf"], workspace=h["ws"],
-            **req.scan)
-        wf.envelope(h["bf"], out=h["env"], frame_max=h["fmax"])
-        wf.logclip(h["env"], ref=h["fmax"], db_min=req.db_min, db_max=req.db_max, out=h["db"])
+        das(h["rf"][:b], req.probe, req.grid, rf_scale=req.rf_scale, out=h["bf"][:b],
+            workspace=h["ws"], **req.scan)
+        wf.envelope(h["bf"][:b], out=h["env"][:b], frame_max=h["fmax"][:b])
+        wf.logclip(h["env"][:b], ref=h["fmax"][:b], db_min=req.db_min, db_max=req.db_max,
+                   out=h["db"][:b])
 
     def create(self, req):
         torch, wf = self.torch, self.wf
         dev = self.device
         g = req.grid
+        B = self.max_batch
+        torch.cuda.set_device(dev)                     # also on a creator thread
         h = {"stream": torch.cuda.Stream(device=dev)}
-        h["rf"] = torch.empty(req.rf_host.shape, dtype=req.rf_host.dtype, device=dev)
-        h["ws"] = torch.empty(wf.das_workspace_bytes(req.probe, g, 1, req.rf_host.shape[1]),
+        h["rf"] = torch.empty((B,) + tuple(req.rf_host.shape[1:]), dtype=req.rf_host.dtype, device=dev)
+        h["ws"] = torch.empty(wf.das_workspace_bytes(req.probe, g, B, req.rf_host.shape[1]),
                               dtype=torch.uint8, device=dev)
-        h["bf"] = torch.empty(1, g.nz, g.nx, device=dev)
+        h["bf"] = torch.empty(B, g.nz, g.nx, device=dev)
         h["env"] = torch.empty_like(h["bf"])
         h["db"] = torch.empty_like(h["bf"])
-        h["fmax"] = torch.empty(1, device=dev)
-        h["out"] = torch.empty((g.nz, g.nx), dtype=torch.float32, pin_memory=True)
+        h["fmax"] = torch.empty(B, device=dev)
+        h["out"] = torch.empty((B, g.nz, g.nx), dtype=torch.float32, pin_memory=True)
         h["event"] = torch.cuda.Event()
-        h["graph"] = None
+        h["graphs"] = {}
+        h["b"] = 0
         with torch.cuda.stream(h["stream"]):
             h["rf"].zero_()
-            self._pipeline(h, req)          # validates the request and warms the kernels
+            for b in range(1, B + 1):
+                self._pipeline(h, req, b)      # validates the request, plans and warms each size
         h["stream"].synchronize()
         if self.use_graphs:
-            graph = torch.cuda.CUDAGraph()
-            with torch.cuda.graph(graph, stream=h["stream"]):
-                self._pipeline(h, req)
-            h["graph"] = graph
+            for b in range(1, B + 1):
+                graph = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(graph, stream=h["stream"], capture_error_mode="thread_local"):
+                    self._pipeline(h, req, b)
+                h["graphs"][b] = graph
         return h
 
-    def launch(self, h, req):
+    def launch(self, h, reqs):
         torch = self.torch
+        b = len(reqs)
+        if b > self.max_batch:
+            raise ValueError(f"batch of {b} exceeds the slot's {self.max_batch}")
         with torch.cuda.stream(h["stream"]):
-            h["rf"].copy_(req.rf_host, non_blocking=True)
-            if h["graph"] is not None:
-                h["graph"].replay()
+            for i, r in enumerate(reqs):
+                h["rf"][i].copy_(r.rf_host[0], non_blocking=True)
+            if b in h["graphs"]:
+                h["graphs"][b].replay()
             else:
-                self._pipeline(h, req)
-            h["out"].copy_(h["db"][0], non_blocking=True)
+                self._pipeline(h, reqs[0], b)
+            h["out"][:b].copy_(h["db"][:b], non_blocking=True)
             h["event"].record(h["stream"])
+        h["b"] = b
 
     def done(self, h) -> bool:
         return h["event"].query()
 
     def result(self, h):
-        return h["out"].numpy().copy()
+        return [h["out"][i].numpy().copy() for i in range(h["b"])]
 
     def release(self, h):
         h["stream"].synchronize()

@@ -66,6 +66,8 @@ def test_random_rf_sweep_parity(k):
 STAGING_VARIANTS = [
     {},                                              # default: reciprocal pairs, TMA staging
     {"WF_DAS_NO_SYM": "1"},                          # every (t, r) pair on its own trace
+    {"WF_DAS_NO_TMAP": "1"},                         # per-trace bulk copies, reciprocal
+    {"WF_DAS_NO_TMAP": "1", "WF_DAS_NO_SYM": "1"},
     {"WF_DAS_NO_TMA": "1"},                          # register-staged path, reciprocal
     {"WF_DAS_NO_TMA": "1", "WF_DAS_NO_SYM": "1"},
     {"WF_DAS_TILE": "4,2"},                          # 32 x 16 tiles
@@ -84,7 +86,7 @@ def test_staging_variants_agree_with_oracle(mode, monkeypatch):
     want = oracle.das(case, threads=THREADS)
     outs = []
     for env in STAGING_VARIANTS:
-        for k in ("WF_DAS_NO_SYM", "WF_DAS_NO_TMA", "WF_DAS_TILE", "WF_DAS_GROUPS"):
+        for k in ("WF_DAS_NO_SYM", "WF_DAS_NO_TMA", "WF_DAS_NO_TMAP", "WF_DAS_TILE", "WF_DAS_GROUPS"):
             monkeypatch.delenv(k, raising=False)
         for k, v in env.items():
             monkeypatch.setenv(k, v)

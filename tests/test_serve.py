@@ -27,7 +27,7 @@ class FakeExecutor:
 
     def __init__(self, clock, duration=1.0, fail_rids=()):
         self.clock, self.duration, self.fail = clock, duration, set(fail_rids)
-        self.created, self.released, self.launches = 0, 0, []
+        self.created, self.released, self.launches, self.batches = 0, 0, [], []
 
     def footprint(self, req):
         if req.grid.nx <= 0:
@@ -38,20 +38,22 @@ class FakeExecutor:
         if req.grid.nz <= 0:
             raise ValueError("invalid grid")
         self.created += 1
-        return {"done_at": None, "req": None}
+        return {"done_at": None, "reqs": []}
 
-    def launch(self, h, req):
-        if req.rid in self.fail:
+    def launch(self, h, reqs):
+        if any(r.rid in self.fail for r in reqs):
             raise RuntimeError("injected launch failure")
         h["done_at"] = self.clock() + self.duration
-        h["req"] = req
-        self.launches.append((req.rid, self.clock()))
+        h["reqs"] = list(reqs)
+        for r in reqs:
+            self.launches.append((r.rid, self.clock()))
+        self.batches.append([r.rid for r in reqs])
 
     def done(self, h):
         return h["done_at"] is not None and self.clock() >= h["done_at"]
 
     def result(self, h):
-        return np.full((2, 2), float(h["req"].rid))
+        return [np.full((2, 2), float(r.rid)) for r in h["reqs"]]
 
     def release(self, h):
         self.released += 1
@@ -164,3 +166,91 @@ def test_run_feeds_arrivals_in_time_order_and_reports_percentiles():
     assert sorted(res) == list(range(20))
     st = latency_stats(res)
     assert st["n"] == 20 and 0.2 <= st["p50_ms"] / 1e3 <= st["p99_ms"] / 1e3 < 1.0
+
+
+def test_queued_requests_of_a_shape_run_as_one_batch():
+    clock = Clock()
+    ex = FakeExecutor(clock, duration=1.0)
+    s = Server(ex, hbm_budget=1000, max_slots_per_shape=1, clock=clock, max_batch=3)
+    for i in range(5):
+        s.submit(req(i))
+    s.submit(req(9, shape=1))
+    s.step()
+    assert ex.batches == [[0, 1, 2], [9]]            # FIFO within the shape, up to 3 at once
+    clock.t = 1.0
+    s.step()
+    assert ex.batches[-1] == [3, 4]
+    clock.t = 2.0
+    s.step()
+    assert sorted(s.results) == [0, 1, 2, 3, 4, 9]
+    assert all(s.results[i].db[0, 0] == float(i) for i in (0, 1, 2, 3, 4, 9))
+    assert s.results[0].cold and s.results[2].cold and not s.results[3].cold
+
+
+def _wait(pred, timeout=5.0):
+    import time as _t
+    t_end = _t.time() + timeout
+    while not pred() and _t.time() < t_end:
+        _t.sleep(0.001)
+    assert pred()
+
+
+def test_slot_creation_off_the_admission_path():
+    """While a new shape's slot is being built on the creator thread, requests of other
+    shapes keep being admitted and retired; the new shape's requests wait in order."""
+    import threading
+
+    clock = Clock()
+    gate = threading.Event()
+
+    class SlowCreate(FakeExecutor):
+        def create(self, req):
+            if req.probe.n_elements == 9:       # shape 1 takes long to build
+                assert gate.wait(5.0)
+            return super().create(req)
+
+    ex = SlowCreate(clock, duration=1.0)
+    s = Server(ex, hbm_budget=1000, max_slots_per_shape=1, clock=clock, async_create=True)
+    s.submit(req(0, shape=0))
+    _wait(lambda: (s.step(), len(ex.launches) == 1)[1])
+    s.submit(req(1, shape=1))
+    s.submit(req(2, shape=0))
+    s.submit(req(3, shape=1))
+    s.step()                                 # shape 1 creation starts; shape 0's slot is busy
+    clock.t = 1.0
+    _wait(lambda: (s.step(), 2 in [r for r, _ in ex.launches])[1])
+    assert [r for r, _ in ex.launches] == [0, 2]     # shape 0 kept running
+    clock.t = 2.0
+    s.step()
+    assert 2 in s.results and 1 not in s.results
+    gate.set()
+    _wait(lambda: (s.step(), 1 in [r for r, _ in ex.launches])[1])
+    clock.t = 3.0
+    s.step()
+    clock.t = 4.0
+    s.step()
+    assert [r for r, _ in ex.launches] == [0, 2, 1, 3]
+    assert s.results[1].cold and not s.results[3].cold and not s.results[2].cold
+    s.close()
+
+
+def test_failed_slot_creation_rejects_that_shape_only():
+    clock = Clock()
+
+    class FailCreate(FakeExecutor):
+        def create(self, req):
+            if req.probe.n_elements == 9:
+                raise ValueError("geometry refused")
+            return super().create(req)
+
+    ex = FailCreate(clock, duration=1.0)
+    s = Server(ex, hbm_budget=1000, clock=clock, async_create=True)
+    s.submit(req(1, shape=1))
+    s.submit(req(0, shape=0))
+    s.submit(req(2, shape=1))
+    _wait(lambda: (s.step(), 1 in s.results and 2 in s.results)[1])
+    assert s.results[1].error.startswith("rejected") and s.results[2].error.startswith("rejected")
+    clock.t = 1.0
+    s.step()
+    assert s.results[0].error is None
+    s.close()
