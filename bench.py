@@ -53,8 +53,9 @@ def parse():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
                     choices=["stai_full", "stai_small", "pwi_full_i16", "pwi_full_f16", "pwi_batch",
                              "served", "diff_pwi"])
-    ap.add_argument("--rate", type=float, default=200.0, help="served: Poisson arrival rate (req/s)")
-    ap.add_argument("--requests", type=int, default=240, help="served: requests in the stream")
+    ap.add_argument("--rates", default="200,1000,2000",
+                    help="served: Poisson arrival rates (req/s), comma-separated")
+    ap.add_argument("--requests", type=int, default=300, help="served: requests per rate")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="CPU time budget of the oracle sample (cpu_baseline / reference arm)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -667,9 +668,13 @@ def _cpu_model():
 # ----------------------------------------------------------------------------- served stream
 
 def run_served(args):
-    """Mixed STAI/PWI request stream through the continuous-batching server vs the plain
-    one-request-at-a-time FP32 path.  Throughput is taken at saturation (every request
-    queued at t = 0); latency p50/p99 under Poisson arrivals at --rate."""
+    """Mixed STAI/PWI request stream through the continuous-batching server against the plain
+    one-request-at-a-time FP32 path, at several Poisson arrival rates.  Request shapes are
+    drawn from the whole served shape space (every element count, transmit scheme, angle
+    count, record length and grid).  The server starts cold: a shape's first request waits
+    for its slot (allocation, warm-up, graph capture on the creator thread), and those cold
+    requests are reported apart from the warm ones.  Saturation throughput: every request
+    queued at t = 0 once every slot exists."""
     from dataclasses import replace as dc_replace
 
     from paper_1811_01566_gb300.serve import (CudaExecutor, Server, latency_stats,
@@ -677,50 +682,79 @@ def run_served(args):
     from synth import serving
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
-    shapes = serving.shape_pool(8, seed=4)
-    items = serving.stream(args.requests, args.rate, seed=4, shapes=shapes, rf_per_shape=True)
-    poisson = requests_from_stream(items)
-    burst = [dc_replace(r, arrival=0.0) for r in poisson]
-    budget = 24 << 30
-    server = Server(CudaExecutor(dev), hbm_budget=budget, max_slots_per_shape=2)
-    warm = {}
-    for r in poisson:                    # one request per shape builds its slot and graph
-        warm.setdefault(r.key(), r)
-    server.run([dc_replace(r, rid=-1 - i, arrival=0.0) for i, r in enumerate(warm.values())])
-
-    def served(reqs):
+    shapes = serving.all_shapes()
+    rates = [float(r) for r in args.rates.split(",")]
+    budget = 32 << 30
+    ex = CudaExecutor(dev, max_batch=4)
+    server = Server(ex, hbm_budget=budget, max_slots_per_shape=2, max_batch=4, async_create=True,
+                    eager_cold=True)
+    per_rate, all_reqs = [], []
+    rf_cache, pinned = {}, {}
+    t_bench = time.perf_counter()
+    for k, rate in enumerate(rates):
+        items = serving.stream(args.requests, rate, seed=10 + k, shapes=shapes, rf_cache=rf_cache)
+        reqs = requests_from_stream(items, pinned=pinned)
+        for r in reqs:
+            r.rid += 100000 * k
+        all_reqs += reqs
         server.results.clear()
         t0 = time.perf_counter()
-        res = server.run(reqs)
-        return dict(res), time.perf_counter() - t0
-
-    def sequential(reqs):
-        res = run_sequential(reqs, dev, as_float32=True)
-        return res, max(res[q.rid].latency + q.arrival for q in reqs)
-
-    sat, sat_span = served(burst)
-    lat, _ = served(poisson)
-    errors = sum(1 for r in list(sat.values()) + list(lat.values()) if r.error)
+        res = dict(server.run(reqs))
+        span = time.perf_counter() - t0
+        seq = run_sequential(reqs, dev, as_float32=True)
+        st, stw, stc, sst = (latency_stats(res), latency_stats(res, cold=False),
+                             latency_stats(res, cold=True), latency_stats(seq))
+        per_rate.append({
+            "rate_req_per_s": rate, "requests": len(reqs),
+            "frames_per_s": round(len(reqs) / span, 2),
+            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+            "warm": {"n": stw["n"], "p50_ms": stw["p50_ms"], "p99_ms": stw["p99_ms"]},
+            "cold": {"n": stc["n"], "p50_ms": stc["p50_ms"], "p99_ms": stc["p99_ms"]},
+            "errors": sum(1 for r in res.values() if r.error),
+            "sequential_fp32": {"frames_per_s": round(len(reqs) / max(r.latency + q.arrival
+                                                                       for q in reqs
+                                                                       for r in [seq[q.rid]]), 2),
+                                "p50_ms": sst["p50_ms"], "p99_ms": sst["p99_ms"]},
+        })
+    # saturation: a burst of the last stream with every slot already built
+    burst = [dc_replace(r, rid=r.rid + 1000000, arrival=0.0) for r in all_reqs[-args.requests:]]
+    server.run([dc_replace(r, rid=r.rid + 2000000) for r in burst])   # slots for every shape
+    server.results.clear()
+    t0 = time.perf_counter()
+    sat = dict(server.run(burst))
+    sat_span = time.perf_counter() - t0
+    seq_sat = run_sequential(burst, dev, as_float32=True)
+    seq_span = max(r.latency for r in seq_sat.values())
+    n_slots, evictions = len(server.slots), server.evictions
     server.close()
-    seq_sat, seq_span = sequential(burst)
-    seq_lat, _ = sequential(poisson)
-    st, sst = latency_stats(lat), latency_stats(seq_lat)
-    n = len(poisson)
+
+    def rnd(d):
+        return {k: (round(v, 3) if isinstance(v, float) else rnd(v) if isinstance(v, dict) else v)
+                for k, v in d.items()}
+
+    for pr_ in per_rate:
+        pr_.update(rnd({k: pr_[k] for k in ("p50_ms", "p99_ms", "warm", "cold", "sequential_fp32")}))
     return {
-        "metric": "served frames/s (mixed STAI/PWI B-mode stream, int16 RF)",
-        "value": round(n / sat_span, 2), "unit": "frames/s", "n_gpus": 1,
+        "metric": "served frames/s and p50/p99 latency (mixed STAI/PWI B-mode stream, int16 RF)",
+        "value": round(len(burst) / sat_span, 2), "unit": "frames/s", "n_gpus": 1,
         "higher_is_better": True, "data": "synthetic", "dtype": "f32",
-        "config": {"workload": f"served: {len(shapes)} shapes from E in {{64,128,192}}, angles in "
-                               f"{{1,16,64}}, samples in {{1024,2048,4096}}, grids 256x256..1024x512, "
-                               f"{n} requests; throughput with all queued at t=0, latency under "
-                               f"Poisson {args.rate} req/s",
-                   "hbm_budget_bytes": budget, "slots_per_shape": 2, "launch": "CUDA graph per slot",
-                   "timing": "host wall clock from arrival to completion seen by the loop; "
-                             "includes pinned H2D of the RF and D2H of the dB image"},
-        "p50_ms": round(st["p50_ms"], 3), "p99_ms": round(st["p99_ms"], 3), "errors": errors,
-        "sequential_fp32": {"value": round(n / seq_span, 2), "unit": "frames/s",
-                            "p50_ms": round(sst["p50_ms"], 3), "p99_ms": round(sst["p99_ms"], 3)},
-        "shapes": shapes,
+        "config": {"workload": f"served: requests drawn uniformly from all {len(shapes)} shapes of "
+                               f"E in {{64,128,192}} x (STAI, PWI with {{1,16,64}} angles) x samples "
+                               f"{{1024,2048,4096}} x grids {{256x256,512x256,512x512,1024x512}}; "
+                               f"{args.requests} requests per rate; value = saturation (all queued "
+                               f"at t=0, every slot built)",
+                   "hbm_budget_bytes": budget, "slots_per_shape": 2,
+                   "max_batch": "4 requests of a shape per launch while their RF stays within 64 MiB",
+                   "slot_creation": "creator thread (allocation, warm-up, graph capture per batch size); "
+                                    "a shape's requests arriving while its slot is built run at once "
+                                    "through eager library calls with temporary buffers (cold)",
+                   "launch": "CUDA graph per slot and batch size",
+                   "timing": "host wall clock from arrival to completion seen by the loop; includes "
+                             "pinned H2D of the RF and D2H of the dB image"},
+        "sequential_fp32_saturation": {"value": round(len(burst) / seq_span, 2), "unit": "frames/s"},
+        "rates": per_rate, "slots_at_end": n_slots, "evictions": evictions,
+        "errors": sum(1 for r in sat.values() if r.error),
+        "seconds": round(time.perf_counter() - t_bench, 1),
     }
 
 
@@ -808,7 +842,8 @@ def run_diff(args):
         "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"diff_pwi: {WORKLOAD_TEXT['diff_pwi']}", "frames_per_step": b,
-                   "launch": "eager autograd step (the sound speed is read on the host each step)"},
+                   "launch": "eager autograd step; the sound speed's host value is re-read only "
+                             "when its tensor changes (not in this loop: no device-to-host sync)"},
         "stages_ms": {n: round(v, 4) for n, v in acc.items()},
         "g_terms_per_s": {"das_forward_contributing": round(fwd_rate / 1e9, 2),
                           "das_backward_contributing": round(bwd_rate / 1e9, 2)},

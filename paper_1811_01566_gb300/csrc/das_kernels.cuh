@@ -374,7 +374,10 @@ template <> struct Seg<int16_t> {
     int nxt;
     __device__ __forceinline__ float at(int k) const {
         const unsigned w = (k >> 1) == 0 ? v.x : (k >> 1) == 1 ? v.y : (k >> 1) == 2 ? v.z : v.w;
-        return (float)((k & 1) ? ((int)w >> 16) : (int)(short)(w & 0xffffu));
+        // exact int16 -> float without a conversion instruction: 1.5 * 2^23 + v has v in its
+        // low mantissa bits (|v| < 2^15), so subtracting 1.5 * 2^23 leaves exactly v
+        const int iv = (k & 1) ? ((int)w >> 16) : ((int)(w << 16) >> 16);
+        return __int_as_float(kMagicBits + iv) - kMagic;
     }
 };
 template <> struct Seg<__half> {
@@ -543,6 +546,7 @@ __device__ __forceinline__ f32x2 x2_fma(f32x2 a, f32x2 b, f32x2 c) {
 }
 
 constexpr int kTableStages = 256;  // stage-window ring in shared memory
+constexpr int kIssueWarp = 1;      // warp whose lanes issue the staging copies
 constexpr int kTableBatch = 128;   // windows computed per refill (one per thread)
 constexpr int kMaxRing = 4;        // deepest TMA raw-sample ring
 
@@ -763,6 +767,13 @@ __global__ void __launch_bounds__(kThreads, 2) das_tiled_kernel(const __grid_con
         if (TMA) {
             for (int i = 0; i < ring; ++i) mbar_init(&s_bar[i], 1);
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            if (a.use_tmap) {
+                asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<unsigned long long>(&a.tm_rows))
+                             : "memory");
+                if (SYM)
+                    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<unsigned long long>(&a.tm_cols))
+                                 : "memory");
+            }
         }
     }
     __syncthreads();
@@ -791,7 +802,8 @@ __global__ void __launch_bounds__(kThreads, 2) das_tiled_kernel(const __grid_con
                 T* slot = raw + (size_t)(qq % ring) * kRawRows * RW;
                 const int r0s = er.x + si.k() * kC, fr = b * a.n_tx;
                 const unsigned box = (unsigned)(kC * RW) * (unsigned)sizeof(T);
-                fence_async_shared();
+                // the slot's previous contents were read by every thread before the last CTA
+                // barrier; a tensor copy's writes need no proxy fence after generic reads
                 mbar_arrive_expect(bar, SYM ? 2u * box : box);
                 tensor_copy_4d(slot, &a.tm_rows, 0, si.lo >> 3, r0s, fr + t, bar);
                 if (SYM) tensor_copy_4d(slot + kC * RW, &a.tm_cols, 0, si.lo >> 3, t, fr + r0s, bar);
@@ -839,7 +851,7 @@ __global__ void __launch_bounds__(kThreads, 2) das_tiled_kernel(const __grid_con
     const f32x2 kMagic2 = x2_pack(kMagic, kMagic);
 
     if (TMA) {
-        if (warp == 0)
+        if (warp == kIssueWarp)
             for (int qq = 0; qq < min(ahead, n_live); ++qq) issue(qq);
     } else if (n_live > 0) {
         const Stage s0 = st[0];
@@ -849,6 +861,14 @@ __global__ void __launch_bounds__(kThreads, 2) das_tiled_kernel(const __grid_con
 
     int k_cur = -1;
     for (int q = 0; q < n_live; ++q) {
+        if (TMA) {
+            // Stage q + ahead goes to ring slot (q - 1) % ring, whose raw samples every thread
+            // converted before the previous barrier.  Issued by warp kIssueWarp before the
+            // conversion of stage q: warps 1, 3, 5, 7 have no conversion work when a window
+            // has at most 32 segments, so the copy issue leaves the stage's critical path.
+            need(q + ahead);
+            if (warp == kIssueWarp && q + ahead < n_live) issue(q + ahead);
+        }
         const Stage si = st[q & (kTableStages - 1)];
         const int k = si.k();
         const int r0 = er.x + k * kC;
@@ -897,16 +917,14 @@ __global__ void __launch_bounds__(kThreads, 2) das_tiled_kernel(const __grid_con
             // (bounded), and leave the stage loop together.
             if (tid == 0) {
                 flag(a.hdr, 4u, (unsigned)blockIdx.x, (unsigned)q, 0u);
-                for (int qq = q + 1; qq < min(q + ahead, n_live); ++qq)
+                for (int qq = q + 1; qq < min(q + ahead + 1, n_live); ++qq)   // issued up to q + ahead
                     mbar_wait_bounded(&s_bar[qq % ring], (unsigned)((qq / ring) & 1));
             }
             break;
         }
-        need(q + ahead);
-        if (q + ahead < n_live) {
-            if (TMA) {
-                if (warp == 0) issue(q + ahead);
-            } else {
+        if (!TMA) {
+            need(q + ahead);
+            if (q + ahead < n_live) {
                 const Stage s1 = st[(q + 1) & (kTableStages - 1)];
                 const int rr0 = er.x + s1.k() * kC;
                 stage_prefetch<T, SYM>(rs, a, rf, s1, tx_of(s1.j()), rr0, min(rr0 + kC - 1, er.y), vec_ok);

@@ -75,7 +75,6 @@ class _Slot:
     busy: list | None = None  # Requests in flight (a batch of one shape)
     last_used: float = 0.0
     pending: object = None    # Future of an asynchronous creation
-    fresh: bool = True        # created for the requests now waiting on it
 
 
 class Server:
@@ -85,11 +84,14 @@ class Server:
     frees up are launched together as one batch.  With ``async_create`` a new
     slot is built on a creator thread (allocation, warm-up, graph capture) while
     the loop keeps admitting and retiring requests of other shapes; the
-    requests of the new shape wait for it in their queue order.
+    requests of the new shape wait for it in their queue order, or, with
+    ``eager_cold``, run at once through the executor's eager path (temporary
+    buffers, no graph) while their slot is being built.
     """
 
     def __init__(self, executor, hbm_budget: int, max_slots_per_shape: int = 4,
-                 clock=time.perf_counter, max_batch: int = 1, async_create: bool = False):
+                 clock=time.perf_counter, max_batch: int = 1, async_create: bool = False,
+                 eager_cold: bool = False):
         self.ex = executor
         self.budget = int(hbm_budget)
         self.max_per_shape = max_slots_per_shape
@@ -103,6 +105,9 @@ class Server:
         self.cancelled: set[int] = set()
         self.failed: dict = {}               # shape key -> creation error
         self.evictions = 0
+        self.eager_cold = eager_cold and async_create
+        self.eager: list = []                # (handle, request, bytes) of cold requests run eagerly
+        self._cold: dict = {}                # rid -> cold when first seen
         self._creator = None
         if async_create:
             from concurrent.futures import ThreadPoolExecutor
@@ -134,6 +139,10 @@ class Server:
         pending = deque()
         queue = list(self.queue)
         taken = [False] * len(queue)
+        ready = {sl.key for sl in self.slots if sl.pending is None}
+        for r in queue:                       # cold: no built slot of its shape when first seen
+            if r.rid not in self._cold:
+                self._cold[r.rid] = r.key() not in ready
         for i, req in enumerate(queue):
             if taken[i]:
                 continue
@@ -151,6 +160,9 @@ class Server:
                 pending.append(req)
                 continue
             slot = self._slot_for(req, key)
+            if slot is None and self.eager_cold and self._creating(key) and self._run_eager(req):
+                launched += 1
+                continue
             if slot is None:
                 blocked_keys.add(key)
                 pending.append(req)
@@ -159,9 +171,12 @@ class Server:
                 self.results[req.rid] = Result(req.rid, latency=self.now() - req.arrival,
                                                error=slot)
                 continue
+            cap = self.max_batch
+            if hasattr(self.ex, "batch_limit"):
+                cap = max(1, min(cap, self.ex.batch_limit(req)))
             batch = [req]
             for j in range(i + 1, len(queue)):   # later queued requests of the same shape
-                if len(batch) >= self.max_batch:
+                if len(batch) >= cap:
                     break
                 r = queue[j]
                 if not taken[j] and r.rid not in self.cancelled and r.key() == key:
@@ -175,12 +190,31 @@ class Server:
                                                  error=f"launch failed: {exc}")
                 continue
             slot.busy = batch
-            slot.cold_batch = slot.fresh
-            slot.fresh = False
             slot.last_used = self.now()
             launched += len(batch)
         self.queue = pending
         return launched
+
+    def _creating(self, key) -> bool:
+        return any(s.key == key and s.pending is not None for s in self.slots)
+
+    def _run_eager(self, req) -> bool:
+        """Run a cold request now on the eager path if its memory fits the budget."""
+        try:
+            need = self.ex.footprint(req, batch=1)
+        except Exception:
+            return False
+        if self.used + need > self.budget:
+            return False
+        try:
+            h = self.ex.launch_eager(req)
+        except Exception as exc:
+            self.results[req.rid] = Result(req.rid, latency=self.now() - req.arrival,
+                                           error=f"launch failed: {exc}")
+            return True
+        self.eager.append((h, req, need))
+        self.used += need
+        return True
 
     def _poll_creations(self):
         for s in list(self.slots):
@@ -195,12 +229,23 @@ class Server:
                 self.used -= s.bytes
 
     def _retire(self):
+        still = []
+        for h, r, need in self.eager:
+            if self.ex.done(h):
+                self._cold.pop(r.rid, None)
+                self.results[r.rid] = Result(r.rid, db=self.ex.result(h)[0],
+                                             latency=self.now() - r.arrival, cold=True)
+                self.ex.release(h)
+                self.used -= need
+            else:
+                still.append((h, r, need))
+        self.eager = still
         for s in self.slots:
             if s.busy is not None and s.pending is None and self.ex.done(s.handle):
                 imgs = self.ex.result(s.handle)
                 for r, img in zip(s.busy, imgs):
                     self.results[r.rid] = Result(r.rid, db=img, latency=self.now() - r.arrival,
-                                                 cold=getattr(s, "cold_batch", False))
+                                                 cold=self._cold.pop(r.rid, False))
                 s.busy = None
                 s.last_used = self.now()
 
@@ -243,7 +288,8 @@ class Server:
 
     # -- driving a schedule -------------------------------------------------------
     def idle(self) -> bool:
-        return not self.queue and all(s.busy is None and s.pending is None for s in self.slots)
+        return (not self.queue and not self.eager and
+                all(s.busy is None and s.pending is None for s in self.slots))
 
     def run(self, requests, poll_sleep: float = 0.0) -> OrderedDict:
         """Feed requests at their arrival times (server clock) until all are answered."""
@@ -259,6 +305,9 @@ class Server:
         return self.results
 
     def close(self):
+        for h, _, _ in self.eager:
+            self.ex.release(h)
+        self.eager = []
         for s in self.slots:
             if s.pending is not None:
                 try:
@@ -291,7 +340,8 @@ class CudaExecutor:
     so a creator thread can build a slot while other streams keep running.
     """
 
-    def __init__(self, device=None, use_graphs: bool = True, max_batch: int = 1):
+    def __init__(self, device=None, use_graphs: bool = True, max_batch: int = 1,
+                 batch_bytes: int = 64 << 20):
         import torch
 
         import paper_1811_01566_gb300 as wf
@@ -299,11 +349,18 @@ class CudaExecutor:
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else device
         self.use_graphs = use_graphs
         self.max_batch = max(1, int(max_batch))
+        self.batch_bytes = int(batch_bytes)
 
-    def footprint(self, req) -> int:
+    def batch_limit(self, req) -> int:
+        """Frames a slot of this shape holds: up to max_batch while their RF stays within
+        batch_bytes (large requests fill the GPU alone and are not batched)."""
+        rf = req.rf_host[0].numel() * req.rf_host.element_size()
+        return max(1, min(self.max_batch, self.batch_bytes // max(rf, 1)))
+
+    def footprint(self, req, batch: int | None = None) -> int:
         wf = self.wf
         n_tx = req.rf_host.shape[1]
-        b = self.max_batch
+        b = self.batch_limit(req) if batch is None else batch
         ws = wf.das_workspace_bytes(req.probe, req.grid, b, n_tx)
         img = req.grid.nz * req.grid.nx * 4
         rf = req.rf_host[0].numel() * req.rf_host.element_size()
@@ -322,7 +379,7 @@ class CudaExecutor:
         torch, wf = self.torch, self.wf
         dev = self.device
         g = req.grid
-        B = self.max_batch
+        B = self.batch_limit(req)
         torch.cuda.set_device(dev)                     # also on a creator thread
         h = {"stream": torch.cuda.Stream(device=dev)}
         h["rf"] = torch.empty((B,) + tuple(req.rf_host.shape[1:]), dtype=req.rf_host.dtype, device=dev)
@@ -352,8 +409,8 @@ class CudaExecutor:
     def launch(self, h, reqs):
         torch = self.torch
         b = len(reqs)
-        if b > self.max_batch:
-            raise ValueError(f"batch of {b} exceeds the slot's {self.max_batch}")
+        if b > h["rf"].shape[0]:
+            raise ValueError(f"batch of {b} exceeds the slot's {h['rf'].shape[0]}")
         with torch.cuda.stream(h["stream"]):
             for i, r in enumerate(reqs):
                 h["rf"][i].copy_(r.rf_host[0], non_blocking=True)
@@ -364,6 +421,23 @@ class CudaExecutor:
             h["out"][:b].copy_(h["db"][:b], non_blocking=True)
             h["event"].record(h["stream"])
         h["b"] = b
+
+    def launch_eager(self, req):
+        """Run one request now without a slot: buffers from the caching allocator on a stream
+        of its own, eager library calls (a cold shape's first requests while its slot is built)."""
+        torch, wf = self.torch, self.wf
+        g = req.grid
+        h = {"stream": torch.cuda.Stream(device=self.device), "event": torch.cuda.Event(), "b": 1}
+        with torch.cuda.stream(h["stream"]):
+            rf = req.rf_host.to(self.device, non_blocking=True)
+            h["rf"] = rf
+            bf, env, db = wf.bmode(rf, req.probe, g, mode=req.mode, rf_scale=req.rf_scale,
+                                   db_min=req.db_min, db_max=req.db_max, **req.scan)
+            h["keep"] = (bf, env, db)
+            h["out"] = torch.empty((1, g.nz, g.nx), dtype=torch.float32, pin_memory=True)
+            h["out"].copy_(db, non_blocking=True)
+            h["event"].record(h["stream"])
+        return h
 
     def done(self, h) -> bool:
         return h["event"].query()
@@ -410,13 +484,14 @@ def run_sequential(requests, device=None, as_float32: bool = True):
     return results
 
 
-def requests_from_stream(items, pin: bool = True):
-    """Marshal stream items (dicts of numpy arrays and SI geometry) into Requests."""
+def requests_from_stream(items, pin: bool = True, pinned: dict | None = None):
+    """Marshal stream items (dicts of numpy arrays and SI geometry) into Requests; ``pinned``
+    (a dict kept by the caller) shares the pinned host copy of an RF record across calls."""
     import torch
 
     import paper_1811_01566_gb300 as wf
     reqs = []
-    pinned = {}
+    pinned = {} if pinned is None else pinned
     for it in items:
         g = it["geometry"]
         rf = it["rf"]

@@ -38,6 +38,19 @@ def shape_pool(n_shapes: int, seed: int, max_samples: int = 4096, max_elements: 
     return shapes
 
 
+def all_shapes(max_samples: int = 4096, max_elements: int = 192):
+    """Every request shape of the served stream: STAI (every element fires) and PWI (each
+    angle count) for every element count, record length and grid."""
+    shapes = []
+    for e in (v for v in ELEMENTS if v <= max_elements):
+        for ns in (v for v in SAMPLES if v <= max_samples):
+            for nz, nx in GRIDS:
+                shapes.append(dict(mode="stai", n_elements=e, n_samples=ns, nz=nz, nx=nx, n_tx=e))
+                for k in ANGLES:
+                    shapes.append(dict(mode="pwi", n_elements=e, n_samples=ns, nz=nz, nx=nx, n_tx=k))
+    return shapes
+
+
 def geometry(shape: dict) -> dict:
     """Probe / grid / scan description of a shape (SI units)."""
     e, ns = shape["n_elements"], shape["n_samples"]
@@ -62,8 +75,12 @@ def rf_noise(shape: dict, seed: int) -> tuple[np.ndarray, float]:
     return q, float(np.float32(1.0 / 32767.0))
 
 
-def stream(n_requests: int, rate_hz: float, seed: int, shapes, rf_per_shape: bool = False):
-    """Requests as dicts: rid, arrival (s, Poisson at rate_hz), shape, geometry, rf, rf_scale."""
+def stream(n_requests: int, rate_hz: float, seed: int, shapes, rf_per_shape: bool = False,
+           rf_cache: dict | None = None):
+    """Requests as dicts: rid, arrival (s, Poisson at rate_hz), shape, geometry, rf, rf_scale.
+
+    rf_per_shape: one noise record per shape; rf_cache (a dict kept by the caller): one
+    record per RF array shape (transmits, elements, samples), shared across streams."""
     rng = np.random.default_rng(seed)
     arrivals = np.cumsum(rng.exponential(1.0 / rate_hz, size=n_requests)) if rate_hz > 0 \
         else np.zeros(n_requests)
@@ -72,7 +89,12 @@ def stream(n_requests: int, rate_hz: float, seed: int, shapes, rf_per_shape: boo
     out = []
     for i in range(n_requests):
         sh = shapes[int(which[i])]
-        if rf_per_shape:
+        if rf_cache is not None:
+            dims = (sh["n_tx"], sh["n_elements"], sh["n_samples"])
+            if dims not in rf_cache:
+                rf_cache[dims] = rf_noise(sh, 1000 + dims[0] * 7 + dims[1] * 13 + dims[2])
+            rf, scale = rf_cache[dims]
+        elif rf_per_shape:
             if int(which[i]) not in cache:
                 cache[int(which[i])] = rf_noise(sh, 1000 + int(which[i]))
             rf, scale = cache[int(which[i])]

@@ -30,8 +30,12 @@ def das_gpu(case, rf=None, workspace=None, out=None):
 
 
 def rel_l2(y, ref):
-    y = np.asarray(y, np.float64)
-    ref = np.asarray(ref, np.float64)
+    """Relative L2 error ||y - ref|| / ||ref|| (real or complex arrays)."""
+    y = np.asarray(y)
+    ref = np.asarray(ref)
+    cplx = np.iscomplexobj(y) or np.iscomplexobj(ref)
+    y = y.astype(np.complex128 if cplx else np.float64)
+    ref = ref.astype(np.complex128 if cplx else np.float64)
     den = np.linalg.norm(ref)
     return float(np.linalg.norm(y - ref) / den) if den > 0 else float(np.linalg.norm(y))
 

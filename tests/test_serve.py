@@ -28,11 +28,18 @@ class FakeExecutor:
     def __init__(self, clock, duration=1.0, fail_rids=()):
         self.clock, self.duration, self.fail = clock, duration, set(fail_rids)
         self.created, self.released, self.launches, self.batches = 0, 0, [], []
+        self.eager = []
 
-    def footprint(self, req):
+    def footprint(self, req, batch=None):
         if req.grid.nx <= 0:
             raise ValueError("invalid grid")
         return req.rf_host.nbytes
+
+    def launch_eager(self, req):
+        h = {"done_at": None, "reqs": []}
+        self.eager.append(req.rid)
+        self.launch(h, [req])
+        return h
 
     def create(self, req):
         if req.grid.nz <= 0:
@@ -184,7 +191,13 @@ def test_queued_requests_of_a_shape_run_as_one_batch():
     s.step()
     assert sorted(s.results) == [0, 1, 2, 3, 4, 9]
     assert all(s.results[i].db[0, 0] == float(i) for i in (0, 1, 2, 3, 4, 9))
-    assert s.results[0].cold and s.results[2].cold and not s.results[3].cold
+    # every request arrived before its shape had a slot: all cold; a later one is warm
+    assert all(s.results[i].cold for i in (0, 1, 2, 3, 4))
+    s.submit(req(5))
+    s.step()
+    clock.t = 3.0
+    s.step()
+    assert not s.results[5].cold
 
 
 def _wait(pred, timeout=5.0):
@@ -230,7 +243,8 @@ def test_slot_creation_off_the_admission_path():
     clock.t = 4.0
     s.step()
     assert [r for r, _ in ex.launches] == [0, 2, 1, 3]
-    assert s.results[1].cold and not s.results[3].cold and not s.results[2].cold
+    # 1 and 3 arrived before their shape's slot existed (cold); 2 found shape 0's slot built
+    assert s.results[1].cold and s.results[3].cold and not s.results[2].cold
     s.close()
 
 
@@ -253,4 +267,37 @@ def test_failed_slot_creation_rejects_that_shape_only():
     clock.t = 1.0
     s.step()
     assert s.results[0].error is None
+    s.close()
+
+
+def test_cold_requests_run_eagerly_while_their_slot_is_built():
+    import threading
+
+    clock = Clock()
+    gate = threading.Event()
+
+    class SlowCreate(FakeExecutor):
+        def create(self, req):
+            assert gate.wait(5.0)
+            return super().create(req)
+
+    ex = SlowCreate(clock, duration=1.0)
+    s = Server(ex, hbm_budget=1000, max_slots_per_shape=1, clock=clock, async_create=True,
+               eager_cold=True)
+    s.submit(req(0, shape=0))
+    s.submit(req(1, shape=0))
+    s.step()                                     # slot creation starts; both run eagerly
+    assert ex.eager == [0, 1] and ex.created == 0
+    clock.t = 1.0
+    s.step()
+    assert s.results[0].cold and s.results[1].cold and s.results[0].error is None
+    assert s.used == 10                          # eager memory returned; the slot being built keeps its share
+    gate.set()
+    _wait(lambda: (s.step(), ex.created == 1 and not s._creating(req(2).key()))[1])
+    s.submit(req(2, shape=0))
+    s.step()
+    assert ex.eager == [0, 1] and [r for r, _ in ex.launches][-1] == 2   # on the built slot
+    clock.t = 2.0
+    s.step()
+    assert not s.results[2].cold
     s.close()
