@@ -704,13 +704,18 @@ def run_served(args):
         seq = run_sequential(reqs, dev, as_float32=True)
         st, stw, stc, sst = (latency_stats(res), latency_stats(res, cold=False),
                              latency_stats(res, cold=True), latency_stats(seq))
+        done_at = [reqs_by_id.arrival + res[rid].latency for rid, reqs_by_id in
+                   ((q.rid, q) for q in reqs) if rid in res and res[rid].error is None]
         per_rate.append({
             "rate_req_per_s": rate, "requests": len(reqs),
-            "frames_per_s": round(len(reqs) / span, 2),
+            "frames_per_s": round(len(done_at) / max(max(done_at) - min(q.arrival for q in reqs),
+                                                     1e-9), 2),
+            "loop_seconds": round(span, 3),
             "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
             "warm": {"n": stw["n"], "p50_ms": stw["p50_ms"], "p99_ms": stw["p99_ms"]},
             "cold": {"n": stc["n"], "p50_ms": stc["p50_ms"], "p99_ms": stc["p99_ms"]},
             "errors": sum(1 for r in res.values() if r.error),
+            "error_messages": sorted({r.error for r in res.values() if r.error})[:3],
             "sequential_fp32": {"frames_per_s": round(len(reqs) / max(r.latency + q.arrival
                                                                        for q in reqs
                                                                        for r in [seq[q.rid]]), 2),
@@ -719,6 +724,7 @@ def run_served(args):
     # saturation: a burst of the last stream with every slot already built
     burst = [dc_replace(r, rid=r.rid + 1000000, arrival=0.0) for r in all_reqs[-args.requests:]]
     server.run([dc_replace(r, rid=r.rid + 2000000) for r in burst])   # slots for every shape
+    server.wait_built()
     server.results.clear()
     t0 = time.perf_counter()
     sat = dict(server.run(burst))

@@ -288,8 +288,8 @@ class Server:
 
     # -- driving a schedule -------------------------------------------------------
     def idle(self) -> bool:
-        return (not self.queue and not self.eager and
-                all(s.busy is None and s.pending is None for s in self.slots))
+        """Nothing queued or in flight (slots still being built for later use do not count)."""
+        return not self.queue and not self.eager and all(s.busy is None for s in self.slots)
 
     def run(self, requests, poll_sleep: float = 0.0) -> OrderedDict:
         """Feed requests at their arrival times (server clock) until all are answered."""
@@ -303,6 +303,12 @@ class Server:
             if poll_sleep:
                 time.sleep(poll_sleep)
         return self.results
+
+    def wait_built(self, poll: float = 0.001) -> None:
+        """Block until every slot being built is ready (or has failed)."""
+        while any(s.pending is not None for s in self.slots):
+            self._poll_creations()
+            time.sleep(poll)
 
     def close(self):
         for h, _, _ in self.eager:
@@ -399,10 +405,18 @@ class CudaExecutor:
                 self._pipeline(h, req, b)      # validates the request, plans and warms each size
         h["stream"].synchronize()
         if self.use_graphs:
+            # CUDAGraph.capture_begin/end directly: the torch.cuda.graph context manager also
+            # synchronises the device, collects garbage and empties the allocator cache, which
+            # would stall every request in flight each time a slot is built.  The pipeline
+            # allocates nothing, so no private memory pool is needed.
             for b in range(1, B + 1):
                 graph = torch.cuda.CUDAGraph()
-                with torch.cuda.graph(graph, stream=h["stream"], capture_error_mode="thread_local"):
-                    self._pipeline(h, req, b)
+                with torch.cuda.stream(h["stream"]):
+                    graph.capture_begin(capture_error_mode="thread_local")
+                    try:
+                        self._pipeline(h, req, b)
+                    finally:
+                        graph.capture_end()
                 h["graphs"][b] = graph
         return h
 
