@@ -400,7 +400,9 @@ template <> struct Seg<float> {
 };
 
 template <typename T> __device__ __forceinline__ float raw_one(int bits);
-template <> __device__ __forceinline__ float raw_one<int16_t>(int bits) { return (float)(short)bits; }
+template <> __device__ __forceinline__ float raw_one<int16_t>(int bits) {
+    return __int_as_float(kMagicBits + (int)(short)bits) - kMagic;   // exact, as Seg<int16_t>::at
+}
 template <> __device__ __forceinline__ float raw_one<__half>(int bits) {
     return __half2float(__ushort_as_half((unsigned short)bits));
 }
@@ -546,7 +548,7 @@ __device__ __forceinline__ f32x2 x2_fma(f32x2 a, f32x2 b, f32x2 c) {
 }
 
 constexpr int kTableStages = 256;  // stage-window ring in shared memory
-constexpr int kIssueWarp = 1;      // warp whose lanes issue the staging copies
+constexpr int kIssueWarp = 7;      // warp whose lanes issue the staging copies
 constexpr int kTableBatch = 128;   // windows computed per refill (one per thread)
 constexpr int kMaxRing = 4;        // deepest TMA raw-sample ring
 
@@ -864,8 +866,9 @@ __global__ void __launch_bounds__(kThreads, 2) das_tiled_kernel(const __grid_con
         if (TMA) {
             // Stage q + ahead goes to ring slot (q - 1) % ring, whose raw samples every thread
             // converted before the previous barrier.  Issued by warp kIssueWarp before the
-            // conversion of stage q: warps 1, 3, 5, 7 have no conversion work when a window
-            // has at most 32 segments, so the copy issue leaves the stage's critical path.
+            // conversion of stage q: the last warp has no conversion work for windows of at
+            // most 28 segments (every plane-wave window), so the copy issue leaves the stage's
+            // critical path.
             need(q + ahead);
             if (warp == kIssueWarp && q + ahead < n_live) issue(q + ahead);
         }
@@ -880,17 +883,28 @@ __global__ void __launch_bounds__(kThreads, 2) das_tiled_kernel(const __grid_con
         if (TMA) {
             stuck = !mbar_wait_bounded(&s_bar[q % ring], (unsigned)((q / ring) & 1));
             if (!stuck) {
-                // raw slot -> FP32 pairs, 8-sample segment kk of trace row c.  Reciprocal
-                // STAI (two traces per row): row c = warp, kk = lane [+ 32], so every warp
-                // takes an equal share; otherwise (c, kk) = (tid >> 6 [+ 4], tid & 63).
+                // raw slot -> FP32 pairs (x[n], x[n+1] - x[n]), one 8-sample segment per thread
+                // and round.  Reciprocal STAI (two traces per row): row c = warp, segment kk =
+                // lane [+ 32].  Otherwise the (row, segment) pairs are numbered row-major and
+                // thread tid takes number tid [+ 256]: a window of up to 32 segments costs each
+                // thread at most one segment (plane-wave windows have at most ~21).
                 static_assert(kThreads / 32 == kC, "one staged trace row per warp");
                 const T* slot = raw + (size_t)(q % ring) * kRawRows * RW;
                 const int nseg = si.len >> 3;
+                const float inv_nseg = 1.0f / (float)nseg;   // row = floor((idx + 0.5) / nseg), exact here
 #pragma unroll
                 for (int i = 0; i < 2; ++i) {
-                    const int c = SYM ? warp : (tid >> 6) + 4 * i;
-                    const int kk = SYM ? lane + 32 * i : tid & 63;
-                    if (kk >= nseg) continue;
+                    int c, kk;
+                    if (SYM) {
+                        c = warp;
+                        kk = lane + 32 * i;
+                        if (kk >= nseg) continue;
+                    } else {
+                        const int idx = tid + kThreads * i;
+                        if (idx >= kC * nseg) continue;
+                        c = (int)(((float)idx + 0.5f) * inv_nseg);
+                        kk = idx - c * nseg;
+                    }
                     float2* dst = buf + c * a.W + 8 * kk;
                     const bool on = r0 + c <= r_last && (!SYM || r0 + c >= t);
                     if (!on) {

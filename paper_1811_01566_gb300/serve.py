@@ -356,6 +356,11 @@ class CudaExecutor:
         self.use_graphs = use_graphs
         self.max_batch = max(1, int(max_batch))
         self.batch_bytes = int(batch_bytes)
+        # Held by a creator thread while it captures a slot's graphs: torch refuses to replay a
+        # graph while any capture is under way, so a launch that finds the lock taken runs the
+        # slot's pipeline with eager calls instead of its graph.
+        import threading
+        self.capture_lock = threading.Lock()
 
     def batch_limit(self, req) -> int:
         """Frames a slot of this shape holds: up to max_batch while their RF stays within
@@ -411,7 +416,7 @@ class CudaExecutor:
             # allocates nothing, so no private memory pool is needed.
             for b in range(1, B + 1):
                 graph = torch.cuda.CUDAGraph()
-                with torch.cuda.stream(h["stream"]):
+                with self.capture_lock, torch.cuda.stream(h["stream"]):
                     graph.capture_begin(capture_error_mode="thread_local")
                     try:
                         self._pipeline(h, req, b)
@@ -428,8 +433,11 @@ class CudaExecutor:
         with torch.cuda.stream(h["stream"]):
             for i, r in enumerate(reqs):
                 h["rf"][i].copy_(r.rf_host[0], non_blocking=True)
-            if b in h["graphs"]:
-                h["graphs"][b].replay()
+            if b in h["graphs"] and self.capture_lock.acquire(blocking=False):
+                try:
+                    h["graphs"][b].replay()
+                finally:
+                    self.capture_lock.release()
             else:
                 self._pipeline(h, reqs[0], b)
             h["out"][:b].copy_(h["db"][:b], non_blocking=True)
