@@ -483,6 +483,7 @@ def run_workload(name, args, rank, world, local_rank, *, with_e2e=True, with_clo
             "unit": "G delay-sums/s",
             "frac": round(gather_achieved / gather_peak, 4),
             "traffic": ncu_traffic(name),
+            "l2_traffic": ncu_traffic(name, "l2_bytes_per_launch"),
             "peak_basis": f"{n_sm} SMs x {SMEM_WORDS_PER_CLOCK} shared-memory words/clock x "
                           f"{clk_mhz:.0f} MHz ({peaks['source']} max SM clock) / "
                           f"{WORDS_PER_DELAY_SUM} words (one FP32 pair) per delay-sum",
@@ -622,8 +623,9 @@ def oracle_frame_nproc(case, threads=None):
     return time.perf_counter() - t0, threads
 
 
-def ncu_traffic(workload):
-    """DRAM bytes per launch of the DAS kernel from the committed ncu summary, or None.
+def ncu_traffic(workload, key="traffic_bytes_per_launch"):
+    """Bytes per launch of the DAS kernel from the committed ncu summary (DRAM read + write by
+    default; key="l2_bytes_per_launch" for the L2 sectors), or None.
 
     The summary records the hash of csrc/das_kernels.cuh (the kernel source) it
     was captured with; a kernel changed since then has no valid traffic figure.
@@ -633,10 +635,11 @@ def ncu_traffic(workload):
     src = os.path.join(ROOT, "paper_1811_01566_gb300", "csrc", "das_kernels.cuh")
     try:
         fields = dict(ln.split(": ", 1) for ln in open(prof).read().splitlines() if ": " in ln
-                      and ln.split(": ", 1)[0] in ("traffic_bytes_per_launch", "source_sha256"))
+                      and ln.split(": ", 1)[0].split(" ")[0] in (key.split(" ")[0], "source_sha256"))
+        fields = {k.split(" ")[0]: v for k, v in fields.items()}
         if fields.get("source_sha256") != hashlib.sha256(open(src, "rb").read()).hexdigest():
             return None
-        return int(fields["traffic_bytes_per_launch"])
+        return int(fields[key.split(" ")[0]])
     except (OSError, KeyError, ValueError):
         return None
 

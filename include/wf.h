@@ -96,8 +96,8 @@ size_t wf_das_workspace_bytes(const wf_probe* probe, const wf_grid* grid, int32_
                               int32_t n_tx_or_angles);
 
 /*
- * STAI delay-and-sum (Sec. II-B "Delay-and-Sum (DAS) beamformer ... Synthetic
- * Transmit Aperture Imaging"; Fig. 2 "Beamforming").  For every pixel p:
+ * STAI delay-and-sum (Sec. II-B: the DAS beamformer for synthetic transmit
+ * aperture imaging; the beamforming block of Fig. 2).  For every pixel p:
  *
  *   b(p) = sum_t w(p, e_t) sum_r w(p, r) lerp(rf[t][r], s(p, t, r))
  *   s(p, t, r) = (|p - x_{e_t}| + |p - x_r|) fs / c - t_start fs      (samples)
@@ -131,7 +131,7 @@ wf_status wf_das_stai(const wf_probe* probe, const wf_grid* grid, int32_t batch,
 
 /*
  * PWI delay-and-sum with coherent compounding over steering angles (Sec. II-B
- * "Plane Wave Imaging").  For every pixel p = (x, z):
+ * names plane-wave imaging).  For every pixel p = (x, z):
  *
  *   b(p) = sum_k sum_r w(p, r) lerp(rf[k][r], s(p, k, r))
  *   s(p, k, r) = (x sin th_k + z cos th_k + |p - x_r|) fs / c - t0_k fs
@@ -247,7 +247,7 @@ wf_status wf_das_backward(const wf_probe* probe, const wf_grid* grid, int32_t mo
                           float* grad_rf, float* grad_weight, float* grad_c, wf_stream stream);
 
 /*
- * Envelope detection (Fig. 2 "Analytic Signal" -> "Absolute Value"; Sec.
+ * Envelope detection (Fig. 2: analytic signal, then absolute value; Sec.
  * II-B: Hilbert transform through the FFT).  For every column x of every
  * frame, with N = nz:
  *
@@ -268,7 +268,7 @@ wf_status wf_envelope(const float* bf, int32_t batch, int32_t nz, int32_t nx, fl
                       float* frame_max, wf_stream stream);
 
 /*
- * Dynamic adjustment (Fig. 2 "Dynamic Adjustment"; Sec. III clips the
+ * Dynamic adjustment (the last block of Fig. 2; Sec. III clips the
  * dynamic range):
  *
  *   out = clamp(20 log10(max(env, 1e-30 ref) / ref), db_min, db_max)
@@ -318,7 +318,7 @@ wf_status wf_logclip_backward(const float* env, int32_t batch, int32_t nz, int32
                               wf_stream stream);
 
 /*
- * Pre-processing (Sec. II-B "Signal Processing Operators": FIR filter).
+ * Pre-processing (Sec. II-B lists a FIR filter among the signal processing operators).
  *
  * wf_fir: every trace (n_samples contiguous values) is filtered by the
  * odd-length FIR h (centre tap at lag 0, zero-phase for symmetric taps):

@@ -135,7 +135,7 @@ double or_lerp(const double* tr, int32_t ns, double s)
 }
 
 /*
- * STAI delay-and-sum (Sec. II-B; Fig. 2 "Beamforming"):
+ * STAI delay-and-sum (Sec. II-B; the beamforming block of Fig. 2):
  *   b(p) = sum_t w(p, e_t) sum_r w(p, r) lerp(rf[t][r], s_stai(p, e_t, r)).
  * Terms whose apodization weight is zero are outside the aperture and are not
  * part of the sum.  Writes rows [row_begin, row_end) of out[nz][nx].
@@ -314,7 +314,7 @@ void or_dft(const double* xr, const double* xi, int32_t n, int32_t inverse,
 }
 
 /*
- * Discrete analytic signal of a real sequence (Fig. 2 "Analytic Signal";
+ * Discrete analytic signal of a real sequence (the analytic-signal block of Fig. 2;
  * Sec. II-B: Hilbert transform built on the FFT).  Reading: the standard
  * one-sided-spectrum construction (Marple 1999): X = DFT(x); H[0] = 1,
  * H[k] = 2 for 0 < k < N/2, H[N/2] = 1 for even N (for odd N, H[k] = 2 for
@@ -340,7 +340,7 @@ void or_analytic(const double* x, int32_t n, double* zr, double* zi)
 
 /*
  * Envelope = |analytic signal| along depth, per image column (Fig. 2
- * "Analytic Signal" then "Absolute Value").  bf and env are [nz][nx];
+ * analytic-signal then absolute-value blocks).  bf and env are [nz][nx];
  * columns [col_begin, col_end) are written.
  */
 void or_envelope(const double* bf, int32_t nz, int32_t nx, int32_t col_begin,
@@ -372,7 +372,7 @@ double or_frame_max(const double* env, int64_t n)
 }
 
 /*
- * Dynamic adjustment (Fig. 2 "Dynamic Adjustment"; Sec. III clips the
+ * Dynamic adjustment (the last block of Fig. 2; Sec. III clips the
  * dynamic range).  Reading: out = clamp(20 log10(max(env, 1e-30 ref) / ref),
  * lo, hi).  A frame whose reference is not positive maps every pixel to lo;
  * a NaN envelope value stays NaN.
@@ -390,7 +390,7 @@ void or_logclip(const double* env, int64_t n, double ref, double lo, double hi, 
 }
 
 /*
- * Reverse mode of the envelope (Fig. 2 "Analytic Signal" -> "Absolute
+ * Reverse mode of the envelope (Fig. 2: analytic signal then absolute
  * Value").  Per column, z = A b with A = F^-1 diag(H) F (F the DFT matrix, H
  * the one-sided-spectrum mask above) and env = |z|.  For a cotangent g of env
  * the cotangent of z is g z / |z| (0 where |z| = 0), and since b is real the
@@ -461,7 +461,7 @@ void or_logclip_backward(const double* env, int64_t n, double ref, int32_t ref_i
 }
 
 /*
- * FIR filtering of one RF trace (pre-processing, Sec. II-B "Signal Processing
+ * FIR filtering of one RF trace (pre-processing, Sec. II-B's signal processing
  * Operators": FIR filter).  Reading: a causal filter of odd length L with its
  * centre tap at lag 0, y[n] = sum_{k=0}^{L-1} h[k] x[n + (L-1)/2 - k], x = 0
  * outside [0, ns); for symmetric (linear-phase) taps this is zero-phase.

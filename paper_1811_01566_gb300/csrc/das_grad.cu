@@ -34,11 +34,16 @@ __device__ __forceinline__ f32x2 x2_mul(f32x2 a, f32x2 b) {
 constexpr int kBwdWCOL = 4;
 constexpr int kBwdP = 2;   // tile 32 x 16 pixels: three weight sets per chunk stay in registers
 
+constexpr int kBwdRing = 3;   // tensor-copy ring depth of the reverse kernel
+
 struct BwdSmem {
-    size_t pairs, gwin, table, elems, ge, total;
+    size_t pairs, gwin, table, elems, ge, raw, total;
 };
 
-__host__ __device__ inline BwdSmem bwd_smem_layout(int W, int n_elements, bool need_rf) {
+// Shared-memory layout of the reverse kernel; with `ring` > 0 a raw ring of that many
+// stage slots ([rows][W + 8] float samples, 128-byte aligned) follows.
+__host__ __device__ inline BwdSmem bwd_smem_layout(int W, int n_elements, bool need_rf, int ring = 0,
+                                                   bool sym = false) {
     BwdSmem L;
     size_t off = 0;
     L.pairs = off;
@@ -51,6 +56,9 @@ __host__ __device__ inline BwdSmem bwd_smem_layout(int W, int n_elements, bool n
     off += (((size_t)n_elements * sizeof(Elem)) + 15) & ~(size_t)15;
     L.ge = off;
     off += (((size_t)n_elements * sizeof(float)) + 15) & ~(size_t)15;
+    off = (off + 127) & ~(size_t)127;
+    L.raw = off;
+    if (ring > 0) off += (size_t)ring * (sym ? 2 : 1) * kC * (W + 8) * sizeof(float) + 128;   // + align slack
     L.total = off;
     return L;
 }
@@ -61,13 +69,19 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
-template <int MODE, bool SYM, bool NEED_RF, bool NEED_PAR>
+template <int MODE, bool SYM, bool NEED_RF, bool NEED_PAR, bool TMA>
 __global__ void __launch_bounds__(kThreads, 2) das_backward_kernel(const __grid_constant__ DasArgs a) {
     static_assert(!SYM || MODE == 0, "reciprocal pairing is an STAI property");
     constexpr int WCOL = kBwdWCOL, P = kBwdP;
+    constexpr int kRawRows = SYM ? 2 * kC : kC;
     using S = Shape<WCOL, P>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const BwdSmem L = bwd_smem_layout(a.W, a.g.n_elements, NEED_RF);
+    const BwdSmem L = bwd_smem_layout(a.W, a.g.n_elements, NEED_RF, TMA ? kBwdRing : 0, SYM);
+    // tensor-copy ring: [kBwdRing][kRawRows][W + 8] raw samples, 128-byte aligned
+    const unsigned raw_pad = (128u - (smem_u32(smem_raw + L.raw) & 127u)) & 127u;
+    float* raw = reinterpret_cast<float*>(smem_raw + L.raw + raw_pad);
+    const int SLOT = kRawRows * (a.W + 8);
+    __shared__ __align__(8) unsigned long long s_bar[kBwdRing];
     float2* buf = reinterpret_cast<float2*>(smem_raw + L.pairs);   // [kC][W] (value, slope)
     int* gw = reinterpret_cast<int*>(smem_raw + L.gwin);           // [kC][W + 8] RF cotangent window (fixed point)
     Stage* st = reinterpret_cast<Stage*>(smem_raw + L.table);      // ring of compacted stages
@@ -164,6 +178,10 @@ __global__ void __launch_bounds__(kThreads, 2) das_backward_kernel(const __grid_
         s_info[0] = n;
         s_info[1] = qa;
         s_info[2] = qb;
+        if (TMA) {
+            for (int i = 0; i < kBwdRing; ++i) mbar_init(&s_bar[i], 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
     }
     __syncthreads();
     const int n_act = s_info[0], q0 = s_info[1], n_stages = s_info[2] - s_info[1];
@@ -177,7 +195,15 @@ __global__ void __launch_bounds__(kThreads, 2) das_backward_kernel(const __grid_
             raw_next += kTableBatch;
         }
     };
-    need(0);
+    constexpr int ahead = TMA ? kBwdRing - 1 : 1;   // stages in flight ahead of the one converted
+    need(ahead - 1);
+    // Copies of stage qq into ring slot qq % kBwdRing (warp kIssueWarp).
+    auto issue = [&](int qq) {
+        const Stage s1 = st[qq & (kTableStages - 1)];
+        const int t1 = tx_of(s1.j()), rr0 = er.x + s1.k() * kC;
+        stage_issue<float, SYM>(a, rf, raw + (size_t)(qq % kBwdRing) * SLOT, s1, t1, rr0,
+                                min(rr0 + kC - 1, er.y), b, &s_bar[qq % kBwdRing], lane);
+    };
 
     // Per receive row c of the chunk, packed pixel pairs (2h, 2h + 1): distance Dr,
     // weight Wr = a_r g_r and window Ar = a_r (PWI: both times the cotangent y, which
@@ -201,25 +227,51 @@ __global__ void __launch_bounds__(kThreads, 2) das_backward_kernel(const __grid_
         }
     };
 
-    if (n_live > 0) {
+    if (TMA) {
+        if (warp == kIssueWarp)
+            for (int qq = 0; qq < min(ahead, n_live); ++qq) issue(qq);
+    } else if (n_live > 0) {
         const Stage s0 = st[0];
         const int rr0 = er.x + s0.k() * kC;
         stage_prefetch<float, SYM>(rs, a, rf, s0, tx_of(s0.j()), rr0, min(rr0 + kC - 1, er.y), vec_ok);
     }
     int k_cur = -1;
     for (int q = 0; q < n_live; ++q) {
+        if (TMA) {
+            // stage q + ahead goes to ring slot (q - 1) % kBwdRing, converted before the
+            // barriers of stage q - 1
+            need(q + ahead);
+            if (warp == kIssueWarp && q + ahead < n_live) issue(q + ahead);
+        }
         const Stage si = st[q & (kTableStages - 1)];
         const int k = si.k();
         const int r0 = er.x + k * kC;
         const int r_last = min(r0 + kC - 1, er.y);
         const int t = tx_of(si.j());
-        stage_store<float, SYM>(rs, buf, a, si, t, r0, r_last);
-        __syncthreads();   // pairs of stage q visible; cotangent window zero
-        need(q + 1);
-        if (q + 1 < n_live) {
-            const Stage s1 = st[(q + 1) & (kTableStages - 1)];
-            const int rr0 = er.x + s1.k() * kC;
-            stage_prefetch<float, SYM>(rs, a, rf, s1, tx_of(s1.j()), rr0, min(rr0 + kC - 1, er.y), vec_ok);
+        bool stuck = false;
+        if (TMA) {
+            stuck = !mbar_wait_bounded(&s_bar[q % kBwdRing], (unsigned)((q / kBwdRing) & 1));
+            if (!stuck) stage_convert<float, SYM>(a, raw + (size_t)(q % kBwdRing) * SLOT, buf, si, t, r0, r_last);
+        } else {
+            stage_store<float, SYM>(rs, buf, a, si, t, r0, r_last);
+        }
+        // pairs of stage q visible; cotangent window zero
+        if (__syncthreads_or(stuck)) {
+            // A copy never completed: let the copies still in flight land (bounded) and leave
+            // the stage loop together; the gradients are then incomplete (the call's result is
+            // unspecified, as for the forward kernels' timeouts).
+            if (tid == 0)
+                for (int qq = q + 1; qq < min(q + ahead + 1, n_live); ++qq)
+                    mbar_wait_bounded(&s_bar[qq % kBwdRing], (unsigned)((qq / kBwdRing) & 1));
+            break;
+        }
+        if (!TMA) {
+            need(q + 1);
+            if (q + 1 < n_live) {
+                const Stage s1 = st[(q + 1) & (kTableStages - 1)];
+                const int rr0 = er.x + s1.k() * kC;
+                stage_prefetch<float, SYM>(rs, a, rf, s1, tx_of(s1.j()), rr0, min(rr0 + kC - 1, er.y), vec_ok);
+            }
         }
         if (k != k_cur) {
             if (k_cur >= 0) flush_chunk(er.x + k_cur * kC);
@@ -499,23 +551,30 @@ __global__ void __launch_bounds__(256) das_backward_direct_kernel(const __grid_c
     if ((threadIdx.x & 31) == 0 && accC != 0.0f && a.grad_c) atomicAdd(a.grad_c, accC * a.neg_inv_c);
 }
 
-template <int MODE, bool SYM, bool NEED_RF, bool NEED_PAR>
+template <int MODE, bool SYM, bool NEED_RF, bool NEED_PAR, bool TMA>
 wf_status launch_bwd_v(DasArgs& A, const Plan& P, int batch, cudaStream_t st) {
     static unsigned long long smem_set = 0ull;
-    auto kern = das_backward_kernel<MODE, SYM, NEED_RF, NEED_PAR>;
+    auto kern = das_backward_kernel<MODE, SYM, NEED_RF, NEED_PAR, TMA>;
     wf_status s = ensure_smem_limit(kern, kMaxTiledSmem, smem_set);
     if (s != WF_OK) return s;
-    const size_t smem = bwd_smem_layout(A.W, A.g.n_elements, NEED_RF).total;
+    const size_t smem = bwd_smem_layout(A.W, A.g.n_elements, NEED_RF, TMA ? kBwdRing : 0, SYM).total;
     kern<<<dim3(P.n_items, batch), kThreads, smem, st>>>(A);
     return last_launch_status();
 }
 
-template <int MODE, bool SYM>
+template <int MODE, bool SYM, bool TMA>
 wf_status launch_bwd_need(DasArgs& A, const Plan& P, int batch, bool need_rf, bool need_par,
                           cudaStream_t st) {
-    if (need_rf && need_par) return launch_bwd_v<MODE, SYM, true, true>(A, P, batch, st);
-    if (need_rf) return launch_bwd_v<MODE, SYM, true, false>(A, P, batch, st);
-    return launch_bwd_v<MODE, SYM, false, true>(A, P, batch, st);
+    if (need_rf && need_par) return launch_bwd_v<MODE, SYM, true, true, TMA>(A, P, batch, st);
+    if (need_rf) return launch_bwd_v<MODE, SYM, true, false, TMA>(A, P, batch, st);
+    return launch_bwd_v<MODE, SYM, false, true, TMA>(A, P, batch, st);
+}
+
+// Whether the tensor-copy staging applies: descriptors made for this call (use_tmap) and
+// the raw ring fits beside the rest of the reverse kernel's shared memory.
+bool backward_tma_fits(const DasArgs& A, bool need_rf, bool sym) {
+    return A.use_tmap &&
+           bwd_smem_layout(A.W, A.g.n_elements, need_rf, kBwdRing, sym).total <= 113 * 1024;
 }
 
 bool backward_is_tiled(const Plan& P, int n_elements, bool need_rf) {
@@ -532,8 +591,13 @@ wf_status launch_das_backward(DasArgs& A, const Plan& P, int batch, bool need_rf
         das_backward_direct_kernel<MODE><<<grid, 256, 0, st>>>(A);
         return last_launch_status();
     }
-    if (MODE == 0 && P.sym) return launch_bwd_need<MODE, MODE == 0>(A, P, batch, need_rf, need_par, st);
-    return launch_bwd_need<MODE, false>(A, P, batch, need_rf, need_par, st);
+    if (MODE == 0 && P.sym)
+        return backward_tma_fits(A, need_rf, true)
+                   ? launch_bwd_need<MODE, MODE == 0, true>(A, P, batch, need_rf, need_par, st)
+                   : launch_bwd_need<MODE, MODE == 0, false>(A, P, batch, need_rf, need_par, st);
+    return backward_tma_fits(A, need_rf, false)
+               ? launch_bwd_need<MODE, false, true>(A, P, batch, need_rf, need_par, st)
+               : launch_bwd_need<MODE, false, false>(A, P, batch, need_rf, need_par, st);
 }
 
 template wf_status launch_das_backward<0>(DasArgs&, const Plan&, int, bool, bool, cudaStream_t);

@@ -1,4 +1,4 @@
-// Delay-and-sum beamforming kernels for STAI and PWI (paper Sec. II-B, Fig. 2 "Beamforming").
+// Delay-and-sum beamforming kernels for STAI and PWI (paper Sec. II-B; the beamforming block of Fig. 2).
 //
 // b(p) = sum_t Wt(p,t) sum_r Wr(p,r) lerp(rf[t][r], Dt(p,t) + Dr(p,r))
 //   STAI: Dt = |p - x_{e_t}| - t_start fs,   Wt = apod(p, e_t) g_{e_t}
@@ -66,9 +66,9 @@ struct GeomDF {
 
 struct DasArgs {
     // TMA descriptors of the RF array viewed as [frames * n_tx][E][ns / 8][8] (dimensions
-    // listed slowest first): boxes of 8 receive rows of one transmit (tm_rows) and of one
-    // receive column of 8 transmits (tm_cols, the mirrored rows of reciprocal STAI), each
-    // (W + 8) samples long.  Filled per call when use_tmap is set.
+    // listed slowest first): boxes of (W + 8) samples of 8 receive rows of one transmit
+    // (tm_rows) and of one receive column of 8 transmits (tm_cols, the mirrored rows of
+    // reciprocal STAI).  Filled per call when use_tmap is set.
     CUtensorMap tm_rows;
     CUtensorMap tm_cols;
     int use_tmap;
@@ -689,6 +689,102 @@ __device__ __forceinline__ int fill_stages(const DasArgs& a, const TileGeo& tg, 
     return total;
 }
 
+// ---------------------------------------------------------------------------
+// Stage staging shared by the forward and reverse tiled kernels: the raw windows of
+// a stage (transmit t, receive chunk r0 .. r_last) go into a ring slot laid out
+// [rows][W + 8] (rows = 8, or 16 with the mirrored traces of reciprocal STAI) and
+// are then converted to FP32 pairs (x[n], x[n+1] - x[n]).
+// ---------------------------------------------------------------------------
+
+// Issue the copies of one stage into `slot`, completion on `bar`; called by every lane of
+// one warp.  Tensor maps: one box per direction, by lane 0 (samples outside the record and
+// rows outside the array arrive as zeros).  Otherwise one bulk copy per trace row (lanes
+// 0..7, mirrored rows lanes 8..15), of the part inside the record.
+template <typename T, bool SYM>
+__device__ __forceinline__ void stage_issue(const DasArgs& a, const T* rf_frame, T* slot, const Stage& si,
+                                            int t, int r0, int r_last, int frame,
+                                            unsigned long long* bar, int lane) {
+    const int BL = a.W + 8;   // raw row stride (samples)
+    if (a.use_tmap) {
+        if (lane == 0) {
+            const int fr = frame * a.n_tx;
+            const unsigned box = (unsigned)(kC * BL) * (unsigned)sizeof(T);
+            // the slot's previous contents were read by every thread before a CTA barrier;
+            // a tensor copy's writes need no proxy fence after generic reads
+            mbar_arrive_expect(bar, SYM ? 2u * box : box);
+            tensor_copy_4d(slot, &a.tm_rows, 0, si.lo >> 3, r0, fr + t, bar);
+            if (SYM) tensor_copy_4d(slot + kC * BL, &a.tm_cols, 0, si.lo >> 3, t, fr + r0, bar);
+        }
+        __syncwarp();
+        return;
+    }
+    const int nrow = r_last - r0 + 1;
+    const int na = max(si.lo, 0), nb = min(si.lo + si.len + 8, a.ns);
+    const int ca = SYM ? max(t - r0, 0) : 0;        // first chunk row paired with t
+    const int cb = SYM ? max(t - r0 + 1, 0) : nrow;  // first row with a mirrored trace
+    const unsigned bytes = nb > na ? (unsigned)((nb - na) * (int)sizeof(T)) : 0u;
+    if (lane == 0) mbar_arrive_expect(bar, bytes * (unsigned)((nrow - ca) + (nrow - cb)));
+    __syncwarp();
+    if (bytes == 0u) return;
+    const long long E = a.g.n_elements;
+    const int c = lane & (kC - 1);
+    if (lane < kC && c >= ca && c < nrow) {
+        fence_async_shared();
+        bulk_copy_g2s(slot + c * BL + (na - si.lo), rf_frame + ((long long)t * E + r0 + c) * a.ns + na,
+                      bytes, bar);
+    } else if (SYM && lane >= kC && lane < 2 * kC && c >= cb && c < nrow) {
+        fence_async_shared();
+        bulk_copy_g2s(slot + (kC + c) * BL + (na - si.lo), rf_frame + ((long long)(r0 + c) * E + t) * a.ns + na,
+                      bytes, bar);
+    }
+}
+
+// Convert the raw windows of a stage in `slot` into FP32 pairs in `buf` ([kC][W]); called by
+// every thread of the CTA (kThreads).  One 8-sample segment per thread and round.
+// Reciprocal STAI (two traces per row): row c = warp, segment kk = lane [+ 32].  Otherwise
+// the (row, segment) pairs are numbered row-major and thread tid takes number tid [+ 256]:
+// a window of up to 32 segments costs each thread at most one segment (plane-wave windows
+// have at most ~21).  Rows outside the chunk, or below the diagonal of a reciprocal pair,
+// are zero.
+template <typename T, bool SYM>
+__device__ __forceinline__ void stage_convert(const DasArgs& a, const T* slot, float2* buf, const Stage& si,
+                                              int t, int r0, int r_last) {
+    static_assert(kThreads / 32 == kC, "one staged trace row per warp");
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int BL = a.W + 8;   // raw row stride (samples)
+    const int nseg = si.len >> 3;
+    const float inv_nseg = 1.0f / (float)nseg;   // row = floor((idx + 0.5) / nseg), exact here
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        int c, kk;
+        if (SYM) {
+            c = warp;
+            kk = lane + 32 * i;
+            if (kk >= nseg) continue;
+        } else {
+            const int idx = tid + kThreads * i;
+            if (idx >= kC * nseg) continue;
+            c = (int)(((float)idx + 0.5f) * inv_nseg);
+            kk = idx - c * nseg;
+        }
+        float2* dst = buf + c * a.W + 8 * kk;
+        const bool on = r0 + c <= r_last && (!SYM || r0 + c >= t);
+        if (!on) {
+            zero_segment(dst);
+        } else {
+            Seg<T> sa;
+            seg_load_smem<T>(sa, slot + c * BL, kk);
+            if (SYM && r0 + c > t) {
+                Seg<T> sb;
+                seg_load_smem<T>(sb, slot + (kC + c) * BL, kk);
+                seg_store_sum<T>(sa, sb, dst, si.lo + 8 * kk, a.ns);
+            } else {
+                seg_store<T>(sa, dst, si.lo + 8 * kk, a.ns);
+            }
+        }
+    }
+}
+
 template <int MODE, typename T, int WCOL, int P, bool DB, bool TMA, bool CHECK, bool SYM>
 __global__ void __launch_bounds__(kThreads, 2) das_tiled_kernel(const __grid_constant__ DasArgs a) {
     static_assert(!SYM || MODE == 0, "reciprocal pairing is an STAI property");
@@ -730,7 +826,7 @@ __global__ void __launch_bounds__(kThreads, 2) das_tiled_kernel(const __grid_con
     const TileGeo tg = tile_geo<S::kCols, S::kRows>(a, txi * S::kCols, tzi * S::kRows);
     const T* rf = reinterpret_cast<const T*>(a.rf) + (long long)b * a.frame_elems;
     const bool vec_ok = (a.ns & 7) == 0;
-    const int RW = a.W + 8;           // raw row stride (samples)
+    const int SLOT = kRawRows * (a.W + 8);          // samples per ring slot: [kRawRows][W + 8]
     const int ring = TMA ? a.ring : 1;
 
     // Pixel offsets from the reference point: column WCOL warp + lx, rows lz + kLR p.
@@ -791,48 +887,13 @@ __global__ void __launch_bounds__(kThreads, 2) das_tiled_kernel(const __grid_con
             raw_next += kTableBatch;
         }
     };
-    // TMA producer (warp 0): raw windows of entry qq into ring slot qq % ring.  Lane 0
-    // posts the byte count, then lane c copies chunk row c (lanes 8 + c: mirrored rows).
+    // TMA producer (warp kIssueWarp): raw windows of entry qq into ring slot qq % ring.
     auto issue = [&](int qq) {
         const Stage si = st[qq & (kTableStages - 1)];
-        unsigned long long* bar = &s_bar[qq % ring];
         const int t = tx_of(si.j());
-        if (a.use_tmap) {
-            // one box of 8 trace rows (and, reciprocal, one of the 8 mirrored rows) per stage;
-            // samples outside the record and rows outside the array arrive as zeros
-            if (lane == 0) {
-                T* slot = raw + (size_t)(qq % ring) * kRawRows * RW;
-                const int r0s = er.x + si.k() * kC, fr = b * a.n_tx;
-                const unsigned box = (unsigned)(kC * RW) * (unsigned)sizeof(T);
-                // the slot's previous contents were read by every thread before the last CTA
-                // barrier; a tensor copy's writes need no proxy fence after generic reads
-                mbar_arrive_expect(bar, SYM ? 2u * box : box);
-                tensor_copy_4d(slot, &a.tm_rows, 0, si.lo >> 3, r0s, fr + t, bar);
-                if (SYM) tensor_copy_4d(slot + kC * RW, &a.tm_cols, 0, si.lo >> 3, t, fr + r0s, bar);
-            }
-            __syncwarp();
-            return;
-        }
-        const int rr0 = er.x + si.k() * kC, nrow = min(rr0 + kC - 1, er.y) - rr0 + 1;
-        const int na = max(si.lo, 0), nb = min(si.lo + si.len + 8, a.ns);
-        const int ca = SYM ? max(t - rr0, 0) : 0;        // first chunk row paired with t
-        const int cb = SYM ? max(t - rr0 + 1, 0) : nrow;  // first row with a mirrored trace
-        const unsigned bytes = nb > na ? (unsigned)((nb - na) * (int)sizeof(T)) : 0u;
-        if (lane == 0) mbar_arrive_expect(bar, bytes * (unsigned)((nrow - ca) + (nrow - cb)));
-        __syncwarp();
-        if (bytes == 0u) return;
-        T* slot = raw + (size_t)(qq % ring) * kRawRows * RW;
-        const long long E = g.n_elements;
-        const int c = lane & (kC - 1);
-        if (lane < kC && c >= ca && c < nrow) {
-            fence_async_shared();
-            bulk_copy_g2s(slot + c * RW + (na - si.lo), rf + ((long long)t * E + rr0 + c) * a.ns + na,
-                          bytes, bar);
-        } else if (SYM && lane >= kC && lane < 2 * kC && c >= cb && c < nrow) {
-            fence_async_shared();
-            bulk_copy_g2s(slot + (kC + c) * RW + (na - si.lo),
-                          rf + ((long long)(rr0 + c) * E + t) * a.ns + na, bytes, bar);
-        }
+        const int rr0 = er.x + si.k() * kC;
+        stage_issue<T, SYM>(a, rf, raw + (size_t)(qq % ring) * SLOT, si, t, rr0, min(rr0 + kC - 1, er.y),
+                            b, &s_bar[qq % ring], lane);
     };
     const int ahead = TMA ? ring - 1 : 1;   // stages in flight ahead of the one being converted
     need(ahead - 1);
@@ -883,44 +944,7 @@ __global__ void __launch_bounds__(kThreads, 2) das_tiled_kernel(const __grid_con
         if (TMA) {
             stuck = !mbar_wait_bounded(&s_bar[q % ring], (unsigned)((q / ring) & 1));
             if (!stuck) {
-                // raw slot -> FP32 pairs (x[n], x[n+1] - x[n]), one 8-sample segment per thread
-                // and round.  Reciprocal STAI (two traces per row): row c = warp, segment kk =
-                // lane [+ 32].  Otherwise the (row, segment) pairs are numbered row-major and
-                // thread tid takes number tid [+ 256]: a window of up to 32 segments costs each
-                // thread at most one segment (plane-wave windows have at most ~21).
-                static_assert(kThreads / 32 == kC, "one staged trace row per warp");
-                const T* slot = raw + (size_t)(q % ring) * kRawRows * RW;
-                const int nseg = si.len >> 3;
-                const float inv_nseg = 1.0f / (float)nseg;   // row = floor((idx + 0.5) / nseg), exact here
-#pragma unroll
-                for (int i = 0; i < 2; ++i) {
-                    int c, kk;
-                    if (SYM) {
-                        c = warp;
-                        kk = lane + 32 * i;
-                        if (kk >= nseg) continue;
-                    } else {
-                        const int idx = tid + kThreads * i;
-                        if (idx >= kC * nseg) continue;
-                        c = (int)(((float)idx + 0.5f) * inv_nseg);
-                        kk = idx - c * nseg;
-                    }
-                    float2* dst = buf + c * a.W + 8 * kk;
-                    const bool on = r0 + c <= r_last && (!SYM || r0 + c >= t);
-                    if (!on) {
-                        zero_segment(dst);
-                    } else {
-                        Seg<T> sa;
-                        seg_load_smem<T>(sa, slot + c * RW, kk);
-                        if (SYM && r0 + c > t) {
-                            Seg<T> sb;
-                            seg_load_smem<T>(sb, slot + (kC + c) * RW, kk);
-                            seg_store_sum<T>(sa, sb, dst, si.lo + 8 * kk, a.ns);
-                        } else {
-                            seg_store<T>(sa, dst, si.lo + 8 * kk, a.ns);
-                        }
-                    }
-                }
+                stage_convert<T, SYM>(a, raw + (size_t)(q % ring) * SLOT, buf, si, t, r0, r_last);
             }
         } else {
             stage_store<T, SYM>(rs, buf, a, si, t, r0, r_last);

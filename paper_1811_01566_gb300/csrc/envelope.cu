@@ -1,5 +1,5 @@
-// Envelope detection: |analytic signal| along depth (paper Fig. 2 "Analytic
-// Signal" -> "Absolute Value"; Sec. II-B builds the Hilbert transform on the FFT).
+// Envelope detection: |analytic signal| along depth (paper Fig. 2: analytic signal,
+// then absolute value; Sec. II-B builds the Hilbert transform on the FFT).
 //
 // For a real column b of length N the analytic signal is b + i h with h the
 // discrete Hilbert transform, h = IDFT(-i sgn(k) DFT(b)) (sgn = 0 at k = 0 and

@@ -1,4 +1,4 @@
-// Pre-processing of RF traces (paper Sec. II-B "Signal Processing Operators":
+// Pre-processing of RF traces (paper Sec. II-B, signal processing operators:
 // FIR filter as the pre-processing op): FIR filtering and IQ demodulation.
 //
 //   FIR:  y[n] = sum_{k<L} h[k] x[n + (L-1)/2 - k]          (odd L, x = 0 outside)

@@ -1,5 +1,5 @@
 // Dynamic adjustment: log compression with dynamic-range clipping (paper
-// Fig. 2 "Dynamic Adjustment"; Sec. III clips the displayed range).
+// the last block of Fig. 2; Sec. III clips the displayed range).
 //
 //   out = clamp(20 log10(max(env, 1e-30 ref) / ref), lo, hi)
 //

@@ -1,5 +1,5 @@
 """Pins of the oracle's pre-processing: FIR filtering and IQ demodulation
-(Sec. II-B "Signal Processing Operators": FIR filter pre-processing).
+(Sec. II-B lists a FIR filter among the signal processing operators).
 
 FIR: the impulse response reproduces the taps, the result equals numpy's
 'same'-mode convolution (a library routine for the same textbook definition),
