@@ -10,9 +10,14 @@
 // one inverse complex FFT of length N give the envelopes of two columns:
 // env_a = sqrt(a^2 + h_a^2), env_b = sqrt(b^2 + h_b^2).
 //
-// Each CTA transforms kPairs column pairs with a radix-2 Stockham FFT in
-// shared memory (twiddles from sincospif of exact arguments 2m/N); the
-// epilogue fuses the magnitude and the per-frame maximum.
+// The forward kernel transforms one to four column pairs per CTA (four pairs:
+// eight adjacent columns, each row of the block one 32-byte sector) with radix-4
+// Stockham passes in shared memory (one radix-2 pass first when log2 N is odd;
+// the formulation of Govindaraju et al., "High performance discrete Fourier
+// transforms on graphics processors", SC 2008); twiddles from sincospif of
+// exact arguments 2m/N; the epilogue fuses the magnitude and the per-frame
+// maximum.  The reverse kernel keeps one column pair per CTA and radix-2 passes.
+#include <algorithm>
 #include <cmath>
 
 #include "common.cuh"
@@ -46,83 +51,154 @@ __device__ __forceinline__ void stockham_pass(const float2* __restrict__ in, flo
     }
 }
 
+// One radix-4 Stockham pass over `cnt` length-N sequences back to back (stride
+// N): span ns, twiddles tw[m] = exp(-2 pi i m / N) for m < 3N/4, conjugated for
+// the inverse.  Input j + r N/4 (r = 0..3) of a sequence is multiplied by
+// w^r, w = exp(-+2 pi i (j mod ns) / (4 ns)), the four go through a DFT of
+// length 4 and land at 4 (j - j mod ns) + (j mod ns) + r ns.
+__device__ __forceinline__ void stockham_pass4(const float2* __restrict__ in, float2* __restrict__ out,
+                                               const float2* __restrict__ tw, int n, int log2n, int ns,
+                                               int cnt, bool inverse) {
+    const int quarter = n >> 2;
+    const int total = quarter * cnt;
+    const int tw_step = quarter / ns;
+    for (int q = threadIdx.x; q < total; q += blockDim.x) {
+        const int seq = q >> (log2n - 2);
+        const int j = q & (quarter - 1);
+        const float2* src = in + seq * n;
+        float2* dst = out + seq * n;
+        const int k = j & (ns - 1);
+        const int m = k * tw_step;
+        float2 w1 = tw[m], w2 = tw[2 * m], w3 = tw[3 * m];
+        if (inverse) {
+            w1.y = -w1.y;
+            w2.y = -w2.y;
+            w3.y = -w3.y;
+        }
+        const float2 v0 = src[j];
+        const float2 u1 = src[j + quarter], u2 = src[j + 2 * quarter], u3 = src[j + 3 * quarter];
+        const float2 v1 = make_float2(u1.x * w1.x - u1.y * w1.y, u1.x * w1.y + u1.y * w1.x);
+        const float2 v2 = make_float2(u2.x * w2.x - u2.y * w2.y, u2.x * w2.y + u2.y * w2.x);
+        const float2 v3 = make_float2(u3.x * w3.x - u3.y * w3.y, u3.x * w3.y + u3.y * w3.x);
+        const float2 a0 = make_float2(v0.x + v2.x, v0.y + v2.y), a1 = make_float2(v0.x - v2.x, v0.y - v2.y);
+        const float2 a2 = make_float2(v1.x + v3.x, v1.y + v3.y), a3 = make_float2(v1.x - v3.x, v1.y - v3.y);
+        // -i a3 (forward) or +i a3 (inverse)
+        const float2 ja3 = inverse ? make_float2(-a3.y, a3.x) : make_float2(a3.y, -a3.x);
+        const int d = ((j - k) << 2) + k;
+        dst[d] = make_float2(a0.x + a2.x, a0.y + a2.y);
+        dst[d + ns] = make_float2(a1.x + ja3.x, a1.y + ja3.y);
+        dst[d + 2 * ns] = make_float2(a0.x - a2.x, a0.y - a2.y);
+        dst[d + 3 * ns] = make_float2(a1.x - ja3.x, a1.y - ja3.y);
+    }
+}
+
+// Full Stockham FFT of `cnt` sequences: a radix-2 pass when log2 n is odd, then radix-4
+// passes.  Returns the buffer holding the result (in or out).
+__device__ __forceinline__ float2* stockham_fft(float2* in, float2* out, const float2* tw, int n,
+                                                int log2n, int cnt, bool inverse) {
+    int ns = 1;
+    if (log2n & 1) {
+        stockham_pass(in, out, tw, n, log2n, ns, cnt, inverse);
+        __syncthreads();
+        float2* t = in; in = out; out = t;
+        ns = 2;
+    }
+    for (; ns < n; ns <<= 2) {
+        stockham_pass4(in, out, tw, n, log2n, ns, cnt, inverse);
+        __syncthreads();
+        float2* t = in; in = out; out = t;
+    }
+    return in;
+}
+
 __device__ __forceinline__ unsigned nonneg_bits(float v) {
     return (v == v && v > 0.0f) ? __float_as_uint(v) : 0u;  // NaN and zero contribute nothing
 }
 
-template <int PAIRS>
-__global__ void __launch_bounds__(kEnvThreads) envelope_kernel(const float* __restrict__ bf,
-                                                               float* __restrict__ env,
-                                                               float* __restrict__ frame_max,
-                                                               int nz, int log2n, int nx) {
+constexpr int kEnvFwdThreads = 512;
+constexpr int kEnvUnroll = 4;
+
+// Forward envelope of `pairs` column pairs (2 * pairs adjacent columns) per CTA.
+__global__ void __launch_bounds__(kEnvFwdThreads) envelope_kernel(const float* __restrict__ bf,
+                                                                  float* __restrict__ env,
+                                                                  float* __restrict__ frame_max, int nz,
+                                                                  int log2n, int nx, int pairs) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = nz;
-    float2* A = reinterpret_cast<float2*>(smem_raw);     // [PAIRS][n]
-    float2* B = A + PAIRS * n;                            // [PAIRS][n]
-    float2* tw = B + PAIRS * n;                           // [n/2]
+    float2* A = reinterpret_cast<float2*>(smem_raw);     // [pairs][n]
+    float2* B = A + pairs * n;                            // [pairs][n]
+    float2* tw = B + pairs * n;                           // [3n/4] (n/2 for n = 2)
     const int b = blockIdx.y;
-    const int x0 = blockIdx.x * (2 * PAIRS);
+    const int cols = 2 * pairs, lc = 31 - __clz(cols);    // columns per CTA (a power of two)
+    const int x0 = blockIdx.x * cols;
     const float* src = bf + (long long)b * nz * nx;
     float* dst = env + (long long)b * nz * nx;
 
-    for (int m = threadIdx.x; m < (n >> 1); m += blockDim.x) {
+    const int ntw = n >= 4 ? 3 * (n >> 2) : (n >> 1);
+    for (int m = threadIdx.x; m < ntw; m += blockDim.x) {
         float s, c;
         sincospif(2.0f * (float)m / (float)n, &s, &c);
         tw[m] = make_float2(c, -s);  // exp(-2 pi i m / n)
     }
-    // Load: pair q holds columns x0 + 2q (real part) and x0 + 2q + 1 (imaginary part).
-    for (int q = threadIdx.x; q < PAIRS * n; q += blockDim.x) {
-        const int pr = q / n, z = q - pr * n;
-        const int xa = x0 + 2 * pr;
-        const float va = xa < nx ? src[(long long)z * nx + xa] : 0.0f;
-        const float vb = xa + 1 < nx ? src[(long long)z * nx + xa + 1] : 0.0f;
-        A[q] = make_float2(va, vb);
+    // Load: element q is row z = q / cols, column x0 + (q mod cols): adjacent threads read adjacent
+    // columns of a row.  Pair p holds columns x0 + 2p (real part) and x0 + 2p + 1 (imaginary part).
+    // kEnvUnroll loads per thread are issued before any is stored, so a small CTA keeps
+    // several global reads in flight instead of waiting out each one in turn.
+    float* Af = reinterpret_cast<float*>(A);
+    const int total = cols * n;
+    for (int q0 = threadIdx.x; q0 < total; q0 += kEnvUnroll * blockDim.x) {
+        float v[kEnvUnroll];
+#pragma unroll
+        for (int u = 0; u < kEnvUnroll; ++u) {
+            const int q = q0 + u * blockDim.x;
+            const int z = q >> lc, x = x0 + (q & (cols - 1));
+            v[u] = (q < total && x < nx) ? src[(long long)z * nx + x] : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < kEnvUnroll; ++u) {
+            const int q = q0 + u * blockDim.x;
+            const int z = q >> lc, c = q & (cols - 1);
+            if (q < total) Af[2 * ((c >> 1) * n + z) + (c & 1)] = v[u];
+        }
     }
     __syncthreads();
-
-    float2* in = A;
-    float2* out = B;
-    for (int ns = 1; ns < n; ns <<= 1) {
-        stockham_pass(in, out, tw, n, log2n, ns, PAIRS, false);
-        __syncthreads();
-        float2* t = in; in = out; out = t;
-    }
-    // Y = DFT(a + i b) is in `in`; form G = -i sgn(k) Y.
-    for (int q = threadIdx.x; q < PAIRS * n; q += blockDim.x) {
+    float2* y = stockham_fft(A, B, tw, n, log2n, pairs, false);
+    float2* other = y == A ? B : A;
+    // Y = DFT(a + i b); form G = -i sgn(k) Y.
+    for (int q = threadIdx.x; q < pairs * n; q += blockDim.x) {
         const int k = q & (n - 1);
-        const float2 y = in[q];
+        const float2 v = y[q];
         float2 gv;
         if (k == 0 || 2 * k == n) gv = make_float2(0.0f, 0.0f);
-        else if (2 * k < n) gv = make_float2(y.y, -y.x);   // -i y
-        else gv = make_float2(-y.y, y.x);                  // +i y
-        in[q] = gv;
+        else if (2 * k < n) gv = make_float2(v.y, -v.x);   // -i y
+        else gv = make_float2(-v.y, v.x);                  // +i y
+        y[q] = gv;
     }
     __syncthreads();
-    for (int ns = 1; ns < n; ns <<= 1) {
-        stockham_pass(in, out, tw, n, log2n, ns, PAIRS, true);
-        __syncthreads();
-        float2* t = in; in = out; out = t;
-    }
-    // in = n * (h_a + i h_b); magnitude epilogue with the original columns.
+    const float2* h = stockham_fft(y, other, tw, n, log2n, pairs, true);
+    // h = n (h_a + i h_b); magnitude epilogue with the original columns, row-major as the load.
     const float inv_n = 1.0f / (float)n;
+    const float* hf = reinterpret_cast<const float*>(h);
     unsigned mx = 0u;
-    for (int q = threadIdx.x; q < PAIRS * n; q += blockDim.x) {
-        const int pr = q / n, z = q - pr * n;
-        const int xa = x0 + 2 * pr;
-        const float2 h = in[q];
-        if (xa < nx) {
-            const float va = src[(long long)z * nx + xa];
-            const float ha = h.x * inv_n;
-            const float e = __fsqrt_rn(fmaf(va, va, ha * ha));
-            dst[(long long)z * nx + xa] = e;
-            mx = max(mx, nonneg_bits(e));
+    for (int q0 = threadIdx.x; q0 < total; q0 += kEnvUnroll * blockDim.x) {
+        float v[kEnvUnroll];
+#pragma unroll
+        for (int u = 0; u < kEnvUnroll; ++u) {
+            const int q = q0 + u * blockDim.x;
+            const int z = q >> lc, x = x0 + (q & (cols - 1));
+            v[u] = (q < total && x < nx) ? src[(long long)z * nx + x] : 0.0f;
         }
-        if (xa + 1 < nx) {
-            const float vb = src[(long long)z * nx + xa + 1];
-            const float hb = h.y * inv_n;
-            const float e = __fsqrt_rn(fmaf(vb, vb, hb * hb));
-            dst[(long long)z * nx + xa + 1] = e;
-            mx = max(mx, nonneg_bits(e));
+#pragma unroll
+        for (int u = 0; u < kEnvUnroll; ++u) {
+            const int q = q0 + u * blockDim.x;
+            const int z = q >> lc, c = q & (cols - 1);
+            const int x = x0 + c;
+            if (q < total && x < nx) {
+                const float hv = hf[2 * ((c >> 1) * n + z) + (c & 1)] * inv_n;
+                const float e = __fsqrt_rn(fmaf(v[u], v[u], hv * hv));
+                dst[(long long)z * nx + x] = e;
+                mx = max(mx, nonneg_bits(e));
+            }
         }
     }
     if (frame_max) {
@@ -251,14 +327,20 @@ extern "C" wf_status wf_envelope(const float* bf, int32_t batch, int32_t nz, int
         wf_status s = cuda_status(cudaMemsetAsync(frame_max, 0, sizeof(float) * batch, st));
         if (s != WF_OK) return s;
     }
-    constexpr int kPairs = 1;
-    const size_t smem = sizeof(float2) * (2 * kPairs * (size_t)nz + nz / 2);
+    // Column pairs per CTA: as many as keep at least ~600 CTAs in flight (four SM-fulls of
+    // 152 SMs), up to four (eight adjacent columns: one 32-byte sector per row), two at
+    // nz = 4096 (shared memory); one thread per radix-4 butterfly of a pass.
+    const long long col_pairs = (long long)batch * ((nx + 1) / 2);
+    int pairs = 1;
+    while (pairs < (nz <= 2048 ? 4 : 2) && col_pairs / (2 * pairs) >= 600) pairs *= 2;
+    const int threads = (int)std::min<long long>(kEnvFwdThreads, std::max<long long>(64, (long long)pairs * nz / 4));
+    const size_t smem = sizeof(float2) * (2 * (size_t)pairs * nz + (nz >= 4 ? 3 * (nz / 4) : nz / 2));
     static unsigned long long smem_set = 0ull;
-    const size_t smem_max = sizeof(float2) * (2 * kPairs * 4096 + 2048);
-    wf_status s = ensure_smem_limit(envelope_kernel<kPairs>, smem_max, smem_set);
+    const size_t smem_max = sizeof(float2) * (2 * 2 * 4096 + 3 * 1024);
+    wf_status s = ensure_smem_limit(envelope_kernel, smem_max, smem_set);
     if (s != WF_OK) return s;
-    dim3 grid((nx + 2 * kPairs - 1) / (2 * kPairs), batch);
-    envelope_kernel<kPairs><<<grid, kEnvThreads, smem, st>>>(bf, env, frame_max, nz, log2n, nx);
+    dim3 grid((nx + 2 * pairs - 1) / (2 * pairs), batch);
+    envelope_kernel<<<grid, threads, smem, st>>>(bf, env, frame_max, nz, log2n, nx, pairs);
     return last_launch_status();
 }
 

@@ -27,11 +27,20 @@ tests exercise it with a fake one on the CPU.
 """
 from __future__ import annotations
 
+import os
 import time
+import traceback
 from collections import OrderedDict, deque
 from dataclasses import dataclass, field
 
 import numpy as np
+
+
+def _describe(exc: BaseException) -> str:
+    """The exception's message and the innermost frame that raised it (file:line function)."""
+    tb = traceback.extract_tb(exc.__traceback__)
+    where = f" [at {os.path.basename(tb[-1].filename)}:{tb[-1].lineno} {tb[-1].name}]" if tb else ""
+    return f"{type(exc).__name__}: {str(exc).strip().splitlines()[0] if str(exc).strip() else ''}{where}"
 
 
 @dataclass
@@ -187,7 +196,7 @@ class Server:
             except Exception as exc:         # a request the library rejects fails alone
                 for r in batch:
                     self.results[r.rid] = Result(r.rid, latency=self.now() - r.arrival,
-                                                 error=f"launch failed: {exc}")
+                                                 error=f"launch failed: {_describe(exc)}")
                 continue
             slot.busy = batch
             slot.last_used = self.now()
@@ -210,7 +219,7 @@ class Server:
             h = self.ex.launch_eager(req)
         except Exception as exc:
             self.results[req.rid] = Result(req.rid, latency=self.now() - req.arrival,
-                                           error=f"launch failed: {exc}")
+                                           error=f"launch failed: {_describe(exc)}")
             return True
         self.eager.append((h, req, need))
         self.used += need
@@ -224,7 +233,7 @@ class Server:
             try:
                 s.handle = fut.result()
             except Exception as exc:
-                self.failed[s.key] = f"rejected: {exc}"
+                self.failed[s.key] = f"rejected: {_describe(exc)}"
                 self.slots.remove(s)
                 self.used -= s.bytes
 
@@ -259,7 +268,7 @@ class Server:
         try:
             need = self.ex.footprint(req)
         except Exception as exc:             # e.g. geometry the library refuses
-            return f"rejected: {exc}"
+            return f"rejected: {_describe(exc)}"
         if need > self.budget:
             return f"rejected: needs {need} bytes of device memory, budget {self.budget}"
         while self.used + need > self.budget:
@@ -280,7 +289,7 @@ class Server:
         try:
             handle = self.ex.create(req)
         except Exception as exc:
-            return f"rejected: {exc}"
+            return f"rejected: {_describe(exc)}"
         slot = _Slot(key, need, handle, last_used=self.now())
         self.slots.append(slot)
         self.used += need
