@@ -268,6 +268,28 @@ wf_status wf_envelope(const float* bf, int32_t batch, int32_t nz, int32_t nx, fl
                       float* frame_max, wf_stream stream);
 
 /*
+ * Envelope detection and dynamic adjustment in one pass (the last two blocks
+ * of Fig. 2) when the caller supplies the per-frame reference: out_db is
+ * wf_logclip(wf_envelope(bf), ref) bit for bit, without the envelope's round
+ * trip through memory.  Without a reference the frame maximum is a whole-frame
+ * dependency: use wf_envelope (with frame_max) and then wf_logclip.
+ *
+ *  bf           device float [batch][nz][nx]; nz a power of two in [2, 4096]
+ *  ref          device float [batch] (required); a reference that is not
+ *               positive maps its frame to db_min, as in wf_logclip
+ *  env          device float [batch][nz][nx] or NULL (not written); may not
+ *               alias bf or out_db
+ *  out_db       device float [batch][nz][nx]; may not alias bf
+ *  frame_max    device float [batch] or NULL: the frames' largest non-NaN
+ *               envelope values, as wf_envelope's
+ * db_min <= db_max.  WF_ERR_INVALID_ARG for a NULL ref / out_db or the
+ * argument errors of wf_envelope.
+ */
+wf_status wf_envelope_logclip(const float* bf, int32_t batch, int32_t nz, int32_t nx,
+                              const float* ref, float db_min, float db_max, float* env,
+                              float* out_db, float* frame_max, wf_stream stream);
+
+/*
  * Dynamic adjustment (the last block of Fig. 2; Sec. III clips the
  * dynamic range):
  *
@@ -491,6 +513,22 @@ wf_status wf_das_plan(const wf_probe* probe, const wf_grid* grid, int32_t mode, 
  * blocks the host.
  */
 wf_status wf_workspace_check(const void* ws, size_t ws_bytes, wf_stream stream);
+
+/*
+ * A CUDA stream of the caller's own (non-blocking with respect to the legacy
+ * default stream) on the calling thread's current device, and its release.
+ * The serving runtime gives every slot one, so that no other work -- a
+ * stream pool handing the same stream to another request, or another
+ * thread -- lands on a stream while a graph is being captured on it.
+ * wf_stream_destroy returns once the stream's pending work is done; the
+ * stream must not be used afterwards, by the caller or by anything that
+ * remembers it (a pinned-memory allocator that records events on the streams
+ * a buffer was copied on, for instance), so long-lived runtimes keep their
+ * streams for reuse instead.  WF_ERR_INVALID_ARG for a NULL out / stream,
+ * WF_ERR_CUDA if the runtime refuses.
+ */
+wf_status wf_stream_create(wf_stream* out);
+wf_status wf_stream_destroy(wf_stream stream);
 
 /* Static, human-readable name of a status code. */
 const char* wf_status_string(wf_status status);

@@ -97,6 +97,8 @@ def _load():
             lib.wf_das_backward.restype = C.c_int
             lib.wf_envelope.argtypes = [vp, i32, i32, i32, vp, vp, vp]
             lib.wf_envelope.restype = C.c_int
+            lib.wf_envelope_logclip.argtypes = [vp, i32, i32, i32, vp, f32, f32, vp, vp, vp, vp]
+            lib.wf_envelope_logclip.restype = C.c_int
             lib.wf_logclip.argtypes = [vp, i32, i32, i32, vp, f32, f32, vp, vp]
             lib.wf_logclip.restype = C.c_int
             lib.wf_envelope_backward.argtypes = [vp, i32, i32, i32, vp, vp, vp]
@@ -133,6 +135,10 @@ def _load():
             lib.wf_das_reload_tuning.restype = C.c_int
             lib.wf_workspace_check.argtypes = [vp, sz, vp]
             lib.wf_workspace_check.restype = C.c_int
+            lib.wf_stream_create.argtypes = [C.POINTER(vp)]
+            lib.wf_stream_create.restype = C.c_int
+            lib.wf_stream_destroy.argtypes = [vp]
+            lib.wf_stream_destroy.restype = C.c_int
             lib.wf_status_string.argtypes = [C.c_int]
             lib.wf_status_string.restype = C.c_char_p
             lib.wf_version.argtypes = []
@@ -558,6 +564,26 @@ def logclip(env: torch.Tensor, *, ref: torch.Tensor | None = None, db_min: float
     return out
 
 
+def envelope_logclip(bf: torch.Tensor, ref: torch.Tensor, *, db_min: float = -60.0, db_max: float = 0.0,
+                     out: torch.Tensor | None = None, env: torch.Tensor | None = None,
+                     frame_max: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """logclip(envelope(bf), ref) in one pass for a caller's per-frame reference ref [batch];
+    env and frame_max (optional) also receive the envelope and the frames' maxima."""
+    if bf.dim() == 2:
+        bf = bf.unsqueeze(0)
+    if not (bf.is_cuda and bf.dtype == torch.float32 and bf.is_contiguous()):
+        raise ValueError("bf must be a contiguous CUDA float32 tensor")
+    b, nz, nx = bf.shape
+    if not (ref.is_cuda and ref.dtype == torch.float32 and ref.numel() == b and ref.is_contiguous()):
+        raise ValueError("ref must be a contiguous CUDA float32 [batch] tensor")
+    out = torch.empty_like(bf) if out is None else out
+    st = _load().wf_envelope_logclip(bf.data_ptr(), b, nz, nx, ref.data_ptr(), float(db_min), float(db_max),
+                                     None if env is None else env.data_ptr(), out.data_ptr(),
+                                     None if frame_max is None else frame_max.data_ptr(), _stream(stream))
+    _check(st, "wf_envelope_logclip")
+    return out
+
+
 def _frames3(t: torch.Tensor, name: str) -> torch.Tensor:
     if t.dim() == 2:
         t = t.unsqueeze(0)
@@ -679,16 +705,40 @@ def iq_demod(rf: torch.Tensor, f0: float, fs: float, taps, *, decim: int = 1,
 
 
 def bmode(rf: torch.Tensor, probe: Probe, grid: Grid, *, mode: str, db_min: float = -60.0,
-          db_max: float = 0.0, workspace: torch.Tensor | None = None, stream=None, **scan):
-    """Whole Fig. 2 pipeline: returns (beamformed, envelope, dB image), each [batch, nz, nx]."""
+          db_max: float = 0.0, ref: torch.Tensor | None = None, workspace: torch.Tensor | None = None,
+          stream=None, **scan):
+    """Whole Fig. 2 pipeline: returns (beamformed, envelope, dB image), each [batch, nz, nx].
+    ref None: each frame against its own maximum; a CUDA float32 [batch] ref (a fixed display
+    reference) runs envelope and log-clip as one fused pass."""
     if mode == "stai":
         bf = das_stai(rf, probe, grid, workspace=workspace, stream=stream, **scan)
     elif mode == "pwi":
         bf = das_pwi(rf, probe, grid, workspace=workspace, stream=stream, **scan)
     else:
         raise ValueError("mode must be 'stai' or 'pwi'")
+    if ref is not None:
+        env = torch.empty_like(bf)
+        db = envelope_logclip(bf, ref, db_min=db_min, db_max=db_max, env=env, stream=stream)
+        return bf, env, db
     env, fmax = envelope(bf, stream=stream)
     return bf, env, logclip(env, ref=fmax, db_min=db_min, db_max=db_max, stream=stream)
+
+
+def stream_create(device=None) -> torch.cuda.ExternalStream:
+    """A CUDA stream of the caller's own (wf_stream_create on `device`, default the current one),
+    wrapped for torch; hand it to stream_destroy when done.  Unlike torch.cuda.Stream(), which
+    draws from a small round-robin pool, no other caller ever receives the same stream."""
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    ptr = C.c_void_p()
+    with torch.cuda.device(dev):
+        _check(_load().wf_stream_create(C.byref(ptr)), "wf_stream_create")
+    return torch.cuda.ExternalStream(ptr.value, device=dev)
+
+
+def stream_destroy(stream: torch.cuda.ExternalStream) -> None:
+    """Wait for the stream's work, then release a stream from stream_create."""
+    with torch.cuda.device(stream.device):
+        _check(_load().wf_stream_destroy(stream.cuda_stream), "wf_stream_destroy")
 
 
 def workspace_check(workspace: torch.Tensor, stream=None) -> None:

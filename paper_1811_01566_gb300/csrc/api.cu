@@ -14,3 +14,22 @@ extern "C" const char* wf_status_string(wf_status s) {
 }
 
 extern "C" int32_t wf_version(void) { return 100; }
+
+extern "C" wf_status wf_stream_create(wf_stream* out) {
+    if (!out) return WF_ERR_INVALID_ARG;
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+        *out = nullptr;
+        return WF_ERR_CUDA;
+    }
+    *out = reinterpret_cast<wf_stream>(s);
+    return WF_OK;
+}
+
+extern "C" wf_status wf_stream_destroy(wf_stream stream) {
+    if (!stream) return WF_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const cudaError_t e1 = cudaStreamSynchronize(s);
+    const cudaError_t e2 = cudaStreamDestroy(s);
+    return e1 == cudaSuccess && e2 == cudaSuccess ? WF_OK : WF_ERR_CUDA;
+}

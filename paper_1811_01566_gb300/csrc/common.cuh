@@ -36,6 +36,18 @@ inline wf_status last_launch_status() {
     return e == cudaSuccess ? WF_OK : WF_ERR_CUDA;
 }
 
+// Log compression with dynamic-range clipping of one envelope value against its frame's
+// reference (the last block of Fig. 2): clamp(20 log10(max(e, 1e-30 ref) / ref), lo, hi);
+// NaN stays NaN, a reference that is not positive gives lo.  Shared by the log-clip kernels
+// and the envelope kernel's fused epilogue, so both give the same bits.
+__device__ __forceinline__ float db_value(float e, float ref, float lo, float hi) {
+    if (e != e) return e;
+    if (!(ref > 0.0f)) return lo;
+    const float v = fmaxf(e, 1e-30f * ref);
+    const float db = 20.0f * log10f(v / ref);
+    return fminf(fmaxf(db, lo), hi);
+}
+
 // Status block at the head of every DAS workspace (device side).
 struct WsHeader {
     unsigned int flags;   // bit 0: staging window overflow, bit 1: gather index out of window

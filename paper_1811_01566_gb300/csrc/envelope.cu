@@ -118,11 +118,15 @@ __device__ __forceinline__ unsigned nonneg_bits(float v) {
 constexpr int kEnvFwdThreads = 512;
 constexpr int kEnvUnroll = 4;
 
-// Forward envelope of `pairs` column pairs (2 * pairs adjacent columns) per CTA.
+// Forward envelope of `pairs` column pairs (2 * pairs adjacent columns) per CTA.  With `db`
+// set the epilogue also writes the log-clipped value against the caller's reference ref[b]
+// (env may then be null).
 __global__ void __launch_bounds__(kEnvFwdThreads) envelope_kernel(const float* __restrict__ bf,
                                                                   float* __restrict__ env,
                                                                   float* __restrict__ frame_max, int nz,
-                                                                  int log2n, int nx, int pairs) {
+                                                                  int log2n, int nx, int pairs,
+                                                                  const float* __restrict__ ref, float lo,
+                                                                  float hi, float* __restrict__ db) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = nz;
     float2* A = reinterpret_cast<float2*>(smem_raw);     // [pairs][n]
@@ -132,7 +136,9 @@ __global__ void __launch_bounds__(kEnvFwdThreads) envelope_kernel(const float* _
     const int cols = 2 * pairs, lc = 31 - __clz(cols);    // columns per CTA (a power of two)
     const int x0 = blockIdx.x * cols;
     const float* src = bf + (long long)b * nz * nx;
-    float* dst = env + (long long)b * nz * nx;
+    float* dst = env ? env + (long long)b * nz * nx : nullptr;
+    float* dbo = db ? db + (long long)b * nz * nx : nullptr;
+    const float rb = db ? __ldg(ref + b) : 0.0f;
 
     const int ntw = n >= 4 ? 3 * (n >> 2) : (n >> 1);
     for (int m = threadIdx.x; m < ntw; m += blockDim.x) {
@@ -196,7 +202,8 @@ __global__ void __launch_bounds__(kEnvFwdThreads) envelope_kernel(const float* _
             if (q < total && x < nx) {
                 const float hv = hf[2 * ((c >> 1) * n + z) + (c & 1)] * inv_n;
                 const float e = __fsqrt_rn(fmaf(v[u], v[u], hv * hv));
-                dst[(long long)z * nx + x] = e;
+                if (dst) dst[(long long)z * nx + x] = e;
+                if (dbo) dbo[(long long)z * nx + x] = db_value(e, rb, lo, hi);
                 mx = max(mx, nonneg_bits(e));
             }
         }
@@ -312,13 +319,17 @@ __global__ void __launch_bounds__(kEnvThreads) envelope_backward_kernel(
 
 using namespace wf;
 
-extern "C" wf_status wf_envelope(const float* bf, int32_t batch, int32_t nz, int32_t nx, float* env,
-                                 float* frame_max, wf_stream stream) {
-    if (!bf || !env || batch < 1 || batch > 65535 || nx < 1 || nz < 2 || nz > 4096)
+namespace {
+
+// Forward launch shared by wf_envelope and wf_envelope_logclip (db set: fused log-clip).
+wf_status envelope_forward(const float* bf, int32_t batch, int32_t nz, int32_t nx, float* env,
+                           float* frame_max, const float* ref, float lo, float hi, float* db,
+                           wf_stream stream) {
+    if (!bf || !(env || db) || batch < 1 || batch > 65535 || nx < 1 || nz < 2 || nz > 4096)
         return WF_ERR_INVALID_ARG;
     if (nz & (nz - 1)) return WF_ERR_INVALID_ARG;
-    if (bf == env) return WF_ERR_INVALID_ARG;
-    if (((uintptr_t)bf & 3u) || ((uintptr_t)env & 3u) || ((uintptr_t)frame_max & 3u))
+    if (bf == env || bf == db) return WF_ERR_INVALID_ARG;
+    if (((uintptr_t)bf & 3u) || ((uintptr_t)env & 3u) || ((uintptr_t)frame_max & 3u) || ((uintptr_t)db & 3u))
         return WF_ERR_INVALID_ARG;
     int log2n = 0;
     while ((1 << log2n) < nz) ++log2n;
@@ -340,8 +351,24 @@ extern "C" wf_status wf_envelope(const float* bf, int32_t batch, int32_t nz, int
     wf_status s = ensure_smem_limit(envelope_kernel, smem_max, smem_set);
     if (s != WF_OK) return s;
     dim3 grid((nx + 2 * pairs - 1) / (2 * pairs), batch);
-    envelope_kernel<<<grid, threads, smem, st>>>(bf, env, frame_max, nz, log2n, nx, pairs);
+    envelope_kernel<<<grid, threads, smem, st>>>(bf, env, frame_max, nz, log2n, nx, pairs, ref, lo, hi, db);
     return last_launch_status();
+}
+
+}  // namespace
+
+extern "C" wf_status wf_envelope(const float* bf, int32_t batch, int32_t nz, int32_t nx, float* env,
+                                 float* frame_max, wf_stream stream) {
+    if (!env) return WF_ERR_INVALID_ARG;
+    return envelope_forward(bf, batch, nz, nx, env, frame_max, nullptr, 0.0f, 0.0f, nullptr, stream);
+}
+
+extern "C" wf_status wf_envelope_logclip(const float* bf, int32_t batch, int32_t nz, int32_t nx,
+                                         const float* ref, float db_min, float db_max, float* env,
+                                         float* out_db, float* frame_max, wf_stream stream) {
+    if (!ref || !out_db || !(db_min <= db_max)) return WF_ERR_INVALID_ARG;
+    if (((uintptr_t)ref & 3u) || (env && env == out_db)) return WF_ERR_INVALID_ARG;
+    return envelope_forward(bf, batch, nz, nx, env, frame_max, ref, db_min, db_max, out_db, stream);
 }
 
 extern "C" wf_status wf_envelope_backward(const float* bf, int32_t batch, int32_t nz, int32_t nx,

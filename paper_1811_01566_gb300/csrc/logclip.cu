@@ -16,14 +16,6 @@ namespace cg = cooperative_groups;
 
 namespace wf {
 
-__device__ __forceinline__ float db_value(float e, float ref, float lo, float hi) {
-    if (e != e) return e;
-    if (!(ref > 0.0f)) return lo;
-    const float v = fmaxf(e, 1e-30f * ref);
-    const float db = 20.0f * log10f(v / ref);
-    return fminf(fmaxf(db, lo), hi);
-}
-
 __global__ void logclip_ref_kernel(const float* __restrict__ env, const float* __restrict__ ref,
                                    long long frame, float lo, float hi, float* __restrict__ out) {
     const int b = blockIdx.y;

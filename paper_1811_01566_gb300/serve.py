@@ -370,6 +370,18 @@ class CudaExecutor:
         # slot's pipeline with eager calls instead of its graph.
         import threading
         self.capture_lock = threading.Lock()
+        # Streams of released slots, handed to the next slots.  Each stream serves one slot at a
+        # time and none is destroyed: torch's pinned-memory allocator records, when a pinned
+        # buffer is freed, an event on every stream that copied it, and a request's pinned RF
+        # can outlive the slot that copied it.
+        self._free_streams = []
+        self._streams_lock = threading.Lock()
+
+    def _take_stream(self):
+        with self._streams_lock:
+            if self._free_streams:
+                return self._free_streams.pop()
+        return self.wf.stream_create(self.device)
 
     def batch_limit(self, req) -> int:
         """Frames a slot of this shape holds: up to max_batch while their RF stays within
@@ -398,10 +410,22 @@ class CudaExecutor:
     def create(self, req):
         torch, wf = self.torch, self.wf
         dev = self.device
+        torch.cuda.set_device(dev)                     # also on a creator thread
+        # A stream of the slot's own: torch.cuda.Stream() draws from a small round-robin pool,
+        # so another slot or an eager request could be handed the stream this slot captures
+        # on, and its work would land in the capture.
+        h = {"stream": self._take_stream(), "own_stream": True}
+        try:
+            return self._build(h, req)
+        except BaseException:
+            self.release(h)
+            raise
+
+    def _build(self, h, req):
+        torch, wf = self.torch, self.wf
+        dev = self.device
         g = req.grid
         B = self.batch_limit(req)
-        torch.cuda.set_device(dev)                     # also on a creator thread
-        h = {"stream": torch.cuda.Stream(device=dev)}
         h["rf"] = torch.empty((B,) + tuple(req.rf_host.shape[1:]), dtype=req.rf_host.dtype, device=dev)
         h["ws"] = torch.empty(wf.das_workspace_bytes(req.probe, g, B, req.rf_host.shape[1]),
                               dtype=torch.uint8, device=dev)
@@ -477,8 +501,13 @@ class CudaExecutor:
         return [h["out"][i].numpy().copy() for i in range(h["b"])]
 
     def release(self, h):
-        h["stream"].synchronize()
+        stream, own = h.get("stream"), h.get("own_stream", False)
+        if stream is not None:
+            stream.synchronize()
         h.clear()
+        if own:
+            with self._streams_lock:
+                self._free_streams.append(stream)
 
 
 def run_sequential(requests, device=None, as_float32: bool = True):

@@ -95,3 +95,36 @@ def test_paper_display_range_is_a_shifted_window():
     a = wf.logclip(env, ref=(fmax * 10 ** (-30 / 20)).contiguous(), db_min=0.0, db_max=30.0)
     b = wf.logclip(env, ref=fmax, db_min=-30.0, db_max=0.0)
     assert torch.allclose(a, b + 30.0, atol=1e-4)
+
+
+@pytest.mark.parametrize("nz,nx,batch", [(2, 3, 1), (64, 33, 2), (512, 256, 1), (1024, 512, 3),
+                                         (4096, 5, 1)])
+def test_fused_envelope_logclip_equals_two_passes(nz, nx, batch):
+    """With a caller reference the fused call gives wf_logclip(wf_envelope(bf), ref) bit for bit,
+    also through its optional envelope and frame-maximum outputs; against the oracle as well."""
+    rng = np.random.default_rng(7 * nz + nx)
+    bf = torch.from_numpy(rng.normal(size=(batch, nz, nx)).astype(np.float32)).cuda()
+    bf[0, 0, 0] = float("nan")
+    ref = torch.from_numpy(rng.uniform(0.5, 4.0, size=batch).astype(np.float32)).cuda()
+    if batch > 1:
+        ref[1] = 0.0                       # a reference that is not positive: db_min everywhere
+    env, fmax = wf.envelope(bf)
+    want = wf.logclip(env, ref=ref, db_min=-50.0, db_max=-3.0)
+    got = wf.envelope_logclip(bf, ref, db_min=-50.0, db_max=-3.0)
+    assert torch.equal(torch.nan_to_num(got, nan=123.0), torch.nan_to_num(want, nan=123.0))
+    assert torch.equal(torch.isnan(got), torch.isnan(want))
+    env2, fmax2 = torch.empty_like(bf), torch.empty(batch, device="cuda")
+    got2 = wf.envelope_logclip(bf, ref, db_min=-50.0, db_max=-3.0, env=env2, frame_max=fmax2)
+    assert torch.equal(torch.nan_to_num(got2, nan=123.0), torch.nan_to_num(want, nan=123.0))
+    assert torch.equal(torch.nan_to_num(env2, nan=123.0), torch.nan_to_num(env, nan=123.0))
+    assert torch.equal(fmax2, fmax)
+    g = got.cpu().numpy()
+    b0 = bf.cpu().numpy().astype(np.float64)
+    for b in range(batch):
+        e = oracle.envelope(b0[b], threads=THREADS)
+        d = oracle.logclip(e, float(ref[b].item()), -50.0, -3.0)
+        ok = np.isfinite(d) & np.isfinite(g[b])   # the NaN column's FFT partner is NaN here only
+        assert ok.sum() >= d.size - 2 * nz
+        assert np.abs(g[b][ok] - d[ok]).max() <= 1e-3
+    with pytest.raises(wf.WfError):
+        wf.envelope_logclip(bf, ref, db_min=0.0, db_max=-1.0)

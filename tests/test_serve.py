@@ -301,3 +301,38 @@ def test_cold_requests_run_eagerly_while_their_slot_is_built():
     s.step()
     assert not s.results[2].cold
     s.close()
+
+
+def test_cuda_executor_reuses_streams_and_never_destroys_them():
+    """A released slot's stream goes to the next slot; none is destroyed, so pinned buffers that
+    outlive a slot never record events on a dead stream (host logic, fake library)."""
+    import torch
+    from paper_1811_01566_gb300.serve import CudaExecutor
+
+    class _Stream:
+        def __init__(self):
+            self.syncs = 0
+
+        def synchronize(self):
+            self.syncs += 1
+
+    class _Wf:
+        created = 0
+
+        def stream_create(self, device=None):
+            _Wf.created += 1
+            return _Stream()
+
+        def stream_destroy(self, stream):
+            raise AssertionError("a slot stream was destroyed")
+
+    ex = CudaExecutor(device=torch.device("cpu"))
+    ex.wf = _Wf()
+    s1, s2 = ex._take_stream(), ex._take_stream()
+    assert s1 is not s2 and _Wf.created == 2
+    h = {"stream": s1, "own_stream": True, "rf": object()}
+    ex.release(h)
+    assert h == {} and s1.syncs == 1
+    assert ex._take_stream() is s1 and _Wf.created == 2      # reused, not created anew
+    ex.release({"stream": s2, "own_stream": False})          # eager handle: pool stream, not kept
+    assert ex._take_stream() is not s2 and _Wf.created == 3
