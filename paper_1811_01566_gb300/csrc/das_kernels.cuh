@@ -1046,14 +1046,16 @@ __global__ void __launch_bounds__(kThreads, 2) das_tiled_kernel(const __grid_con
         }
         if (live) {
             // Per pixel: s = tw + Dr, i = floor(s) by the round-down add of 1.5 * 2^23,
-            // f = s - i, v = x[i] + f (x[i+1] - x[i]), acc += Wr v -- two pixels per
-            // packed instruction (the interpolation itself in scalar FMAs, which read
-            // the gathered pairs where they landed).
-            f32x2 tw2[H], acct2[H];
+            // f = s - i, v = x[i] + f (x[i+1] - x[i]), acc += Wr v -- the delay, floor
+            // and fraction two pixels per packed instruction; the interpolation and the
+            // weighted sum in scalar FMAs, which read the gathered pairs where they landed.
+            f32x2 tw2[H];
+            float accs[P];   // this stage's sums per pixel
 #pragma unroll
             for (int h = 0; h < H; ++h) {
                 tw2[h] = x2_pack(tw[2 * h], tw[2 * h + 1]);
-                acct2[h] = 0ull;
+                accs[2 * h] = 0.0f;
+                accs[2 * h + 1] = 0.0f;
             }
 #pragma unroll
             for (int c = 0; c < kC; ++c) {
@@ -1075,14 +1077,17 @@ __global__ void __launch_bounds__(kThreads, 2) das_tiled_kernel(const __grid_con
                     const float2 a0 = bc[i0], a1 = bc[i1];
                     float f0, f1;
                     x2_unpack(f2, f0, f1);
-                    const f32x2 v2 = x2_pack(fmaf(f0, a0.y, a0.x), fmaf(f1, a1.y, a1.x));
-                    acct2[h] = x2_fma(Wr2[c][h], v2, acct2[h]);
+                    // weight and sum per pixel in scalar FMAs (the same rounding as a packed
+                    // FMA, without re-pairing the two interpolated values into one register pair)
+                    float w0, w1;
+                    x2_unpack(Wr2[c][h], w0, w1);
+                    accs[2 * h] = fmaf(w0, fmaf(f0, a0.y, a0.x), accs[2 * h]);
+                    accs[2 * h + 1] = fmaf(w1, fmaf(f1, a1.y, a1.x), accs[2 * h + 1]);
                 }
             }
 #pragma unroll
             for (int h = 0; h < H; ++h) {
-                float t0, t1;
-                x2_unpack(acct2[h], t0, t1);
+                const float t0 = accs[2 * h], t1 = accs[2 * h + 1];
                 acc[2 * h] = MODE == 0 ? fmaf(wt[2 * h], t0, acc[2 * h]) : acc[2 * h] + t0;
                 acc[2 * h + 1] = MODE == 0 ? fmaf(wt[2 * h + 1], t1, acc[2 * h + 1]) : acc[2 * h + 1] + t1;
             }
