@@ -739,6 +739,17 @@ __device__ __forceinline__ void stage_issue(const DasArgs& a, const T* rf_frame,
     }
 }
 
+// floor(i / n) = (i * ceil(2^16 / n)) >> 16 for every segment count n in 1..64 (a window
+// holds at most kMaxWindow / 8 segments) and every i < 8 n + 256 (checked exhaustively): an
+// integer multiply and shift instead of a reciprocal and two conversions per segment.
+struct RowDiv {
+    unsigned m[kMaxWindow / 8 + 1];
+    constexpr RowDiv() : m{} {
+        for (int n = 1; n <= kMaxWindow / 8; ++n) m[n] = (unsigned)((65536 + n - 1) / n);
+    }
+};
+__constant__ constexpr RowDiv kRowDiv{};
+
 // Convert the raw windows of a stage in `slot` into FP32 pairs in `buf` ([kC][W]); called by
 // every thread of the CTA (kThreads).  One 8-sample segment per thread and round.
 // Reciprocal STAI (two traces per row): row c = warp, segment kk = lane [+ 32].  Otherwise
@@ -753,7 +764,7 @@ __device__ __forceinline__ void stage_convert(const DasArgs& a, const T* slot, f
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int BL = a.W + 8;   // raw row stride (samples)
     const int nseg = si.len >> 3;
-    const float inv_nseg = 1.0f / (float)nseg;   // row = floor((idx + 0.5) / nseg), exact here
+    const unsigned mdiv = kRowDiv.m[nseg];   // row = floor(idx / nseg) = (idx mdiv) >> 16
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
         int c, kk;
@@ -764,7 +775,7 @@ __device__ __forceinline__ void stage_convert(const DasArgs& a, const T* slot, f
         } else {
             const int idx = tid + kThreads * i;
             if (idx >= kC * nseg) continue;
-            c = (int)(((float)idx + 0.5f) * inv_nseg);
+            c = (int)(((unsigned)idx * mdiv) >> 16);
             kk = idx - c * nseg;
         }
         float2* dst = buf + c * a.W + 8 * kk;
