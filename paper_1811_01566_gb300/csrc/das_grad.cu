@@ -431,8 +431,11 @@ __global__ void __launch_bounds__(kThreads, 2) das_backward_kernel(const __grid_
                 // 8, contributions reach n <= len); rows paired with t.  Whole groups inside
                 // the record go out as one 16-byte atomic add, edge groups sample by sample.
                 const int span4 = (si.len + 4) >> 2, nrow = r_last - r0 + 1;
+                // c = i / span4 by one multiply-shift per cell (exact for span4 <= 139 and
+                // i < 8 span4 + 8; span4 <= 129 here) and one division per stage
+                const unsigned mspan = ((1u << 20) + (unsigned)span4 - 1u) / (unsigned)span4;
                 for (int i = tid; i < nrow * span4; i += kThreads) {
-                    const int c = i / span4, m = i - c * span4;
+                    const int c = (int)(((unsigned)i * mspan) >> 20), m = i - c * span4;
                     int4* cell = reinterpret_cast<int4*>(gw + c * GW + 4 * m);
                     const int4 qv = *cell;
                     if ((qv.x | qv.y | qv.z | qv.w) == 0) continue;

@@ -123,19 +123,20 @@ __global__ void __launch_bounds__(kThreads, 2) das_iq_kernel(const __grid_consta
         __syncthreads();
         // staged pairs (y, d) of the chunk's rows; zero where n or n + 1 is outside the record
         const int len = si.len;
-        for (int idx = tid; idx < kC * len; idx += kThreads) {
-            const int c = idx / len, i = idx - c * len;
-            const int n = si.lo + i;
-            float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            if (r0 + c <= r_last && n >= 0 && n + 1 <= a.ns - 1) {
-                const float2* tr = iq + ((long long)t * E + r0 + c) * a.ns + n;
-                const float2 x0 = __ldg(tr), x1 = __ldg(tr + 1), e = rot[i];
-                const float yr = x0.x * e.x - x0.y * e.y, yi = x0.x * e.y + x0.y * e.x;
-                const float zr = x1.x * e.x - x1.y * e.y, zi = x1.x * e.y + x1.y * e.x;
-                v = make_float4(yr, yi, zr - yr, zi - yi);
+#pragma unroll 1
+        for (int c = 0; c < kC; ++c)   // row by row: no division by the run-time window length
+            for (int i = tid; i < len; i += kThreads) {
+                const int n = si.lo + i;
+                float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                if (r0 + c <= r_last && n >= 0 && n + 1 <= a.ns - 1) {
+                    const float2* tr = iq + ((long long)t * E + r0 + c) * a.ns + n;
+                    const float2 x0 = __ldg(tr), x1 = __ldg(tr + 1), e = rot[i];
+                    const float yr = x0.x * e.x - x0.y * e.y, yi = x0.x * e.y + x0.y * e.x;
+                    const float zr = x1.x * e.x - x1.y * e.y, zi = x1.x * e.y + x1.y * e.x;
+                    v = make_float4(yr, yi, zr - yr, zi - yi);
+                }
+                buf[c * a.W + i] = v;
             }
-            buf[c * a.W + i] = v;
-        }
         __syncthreads();
         need(q + 1);
         if (k != k_cur) {

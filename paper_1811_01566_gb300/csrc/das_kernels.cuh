@@ -898,13 +898,13 @@ __global__ void __launch_bounds__(kThreads, 2) das_tiled_kernel(const __grid_con
             raw_next += kTableBatch;
         }
     };
-    // TMA producer (warp kIssueWarp): raw windows of entry qq into ring slot qq % ring.
-    auto issue = [&](int qq) {
+    // TMA producer (warp kIssueWarp): raw windows of entry qq into ring slot qq % ring (slot).
+    auto issue = [&](int qq, int slot) {
         const Stage si = st[qq & (kTableStages - 1)];
         const int t = tx_of(si.j());
         const int rr0 = er.x + si.k() * kC;
-        stage_issue<T, SYM>(a, rf, raw + (size_t)(qq % ring) * SLOT, si, t, rr0, min(rr0 + kC - 1, er.y),
-                            b, &s_bar[qq % ring], lane);
+        stage_issue<T, SYM>(a, rf, raw + (size_t)slot * SLOT, si, t, rr0, min(rr0 + kC - 1, er.y),
+                            b, &s_bar[slot], lane);
     };
     const int ahead = TMA ? ring - 1 : 1;   // stages in flight ahead of the one being converted
     need(ahead - 1);
@@ -926,7 +926,7 @@ __global__ void __launch_bounds__(kThreads, 2) das_tiled_kernel(const __grid_con
 
     if (TMA) {
         if (warp == kIssueWarp)
-            for (int qq = 0; qq < min(ahead, n_live); ++qq) issue(qq);
+            for (int qq = 0; qq < min(ahead, n_live); ++qq) issue(qq, qq);   // ahead < ring
     } else if (n_live > 0) {
         const Stage s0 = st[0];
         const int rr0 = er.x + s0.k() * kC;
@@ -934,7 +934,18 @@ __global__ void __launch_bounds__(kThreads, 2) das_tiled_kernel(const __grid_con
     }
 
     int k_cur = -1;
+    // Ring slot q % ring and mbarrier phase (q / ring) & 1 of stage q, advanced per stage: the
+    // ring depth is a run-time value, and a division by it in every thread and stage cost 4 %
+    // of full PWI.
+    int slot_n = 0;
+    unsigned phase_n = 0u;
     for (int q = 0; q < n_live; ++q) {
+        const int slot_q = slot_n;
+        const unsigned phase_q = phase_n;
+        if (++slot_n == ring) {
+            slot_n = 0;
+            phase_n ^= 1u;
+        }
         if (TMA) {
             // Stage q + ahead goes to ring slot (q - 1) % ring, whose raw samples every thread
             // converted before the previous barrier.  Issued by warp kIssueWarp before the
@@ -942,7 +953,8 @@ __global__ void __launch_bounds__(kThreads, 2) das_tiled_kernel(const __grid_con
             // most 28 segments (every plane-wave window), so the copy issue leaves the stage's
             // critical path.
             need(q + ahead);
-            if (warp == kIssueWarp && q + ahead < n_live) issue(q + ahead);
+            if (warp == kIssueWarp && q + ahead < n_live)
+                issue(q + ahead, slot_q + ahead < ring ? slot_q + ahead : slot_q + ahead - ring);
         }
         const Stage si = st[q & (kTableStages - 1)];
         const int k = si.k();
@@ -953,9 +965,9 @@ __global__ void __launch_bounds__(kThreads, 2) das_tiled_kernel(const __grid_con
         if (si.over() && tid == 0) flag(a.hdr, 1u, (unsigned)blockIdx.x, (unsigned)si.len, (unsigned)a.W);
         bool stuck = false;
         if (TMA) {
-            stuck = !mbar_wait_bounded(&s_bar[q % ring], (unsigned)((q / ring) & 1));
+            stuck = !mbar_wait_bounded(&s_bar[slot_q], phase_q);
             if (!stuck) {
-                stage_convert<T, SYM>(a, raw + (size_t)(q % ring) * SLOT, buf, si, t, r0, r_last);
+                stage_convert<T, SYM>(a, raw + (size_t)slot_q * SLOT, buf, si, t, r0, r_last);
             }
         } else {
             stage_store<T, SYM>(rs, buf, a, si, t, r0, r_last);
