@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
                     choices=["stai_full", "stai_small", "pwi_full_i16", "pwi_full_f16", "pwi_batch",
-                             "served", "diff_pwi"])
+                             "served", "diff_pwi", "pwi_full_iq"])
     ap.add_argument("--rates", default="200,1000,2000",
                     help="served: Poisson arrival rates (req/s), comma-separated")
     ap.add_argument("--requests", type=int, default=300, help="served: requests per rate")
@@ -74,6 +74,9 @@ WORKLOAD_TEXT = {
     "pwi_full_i16": "PWI 64 angles (-16..16 deg) x 128 rx x 4096 int16, 1024 x 512 grid",
     "pwi_full_f16": "PWI 64 angles (-16..16 deg) x 128 rx x 4096 float16, 1024 x 512 grid",
     "pwi_batch": "PWI 16 frames x 16 angles x 128 rx x 2048 float32, 512 x 256 grid 5-30 mm",
+    "pwi_full_iq": "PWI 64 angles (-16..16 deg) x 128 rx x 4096 int16, 1024 x 512 grid, through the "
+                   "IQ path: demodulation at 5 MHz (63-tap low-pass, decimation 4), complex DAS of "
+                   "the 1024-sample baseband traces, |IQ| and log-clip",
     "diff_pwi": "differentiable PWI: 16 frames x 16 angles x 128 rx x 2048 float32, 512 x 256 grid "
                 "5-30 mm; forward DAS + envelope + log-clip, MSE against a target B-mode, backward "
                 "to the RF, 128 element weights and the speed of sound",
@@ -862,6 +865,88 @@ def run_diff(args):
     }
 
 
+def run_iq(args):
+    """The full plane-wave frame through the IQ path, one frame per timed step: wf_iq_demod of
+    the int16 RF, wf_das_pwi_iq, wf_iq_envelope with the frame maximum, wf_logclip."""
+    import numpy as np
+
+    import paper_1811_01566_gb300 as wf
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    case = make_case("pwi_full_i16", str(dev))
+    pr = wf.Probe(case.n_elements, case.pitch, case.fs, case.c, case.f_number, case.apod)
+    gr = wf.Grid(case.nz, case.nx, case.x_min, case.x_max, case.z_min, case.z_max)
+    f0, decim = 5e6, 4
+    n = np.arange(63) - 31
+    cut = 3e6 / case.fs      # low-pass at 3 MHz: the 5 MHz pulse's band after mixing to 0
+    taps = (2 * cut * np.sinc(2 * cut * n) * np.hamming(63)).astype(np.float32)
+    rfs = [torch.from_numpy(case.rf).to(dev) for _ in range(6)]   # 384 MiB > L2
+    m = -(-case.n_samples // decim)
+    img = torch.empty(1, case.nz, case.nx, device=dev, dtype=torch.complex64)
+    ws = torch.empty(wf.das_iq_workspace_bytes(pr, gr, "pwi", batch=1, n_tx=case.n_tx, m=m, decim=decim),
+                     dtype=torch.uint8, device=dev)
+    env = torch.empty(1, case.nz, case.nx, device=dev)
+    fmax = torch.empty(1, device=dev)
+    db = torch.empty_like(env)
+    stream = torch.cuda.current_stream(dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+
+    def step(i, timed=False):
+        if timed: ev[0].record(stream)
+        iq = wf.iq_demod(rfs[i % 6], f0, case.fs, taps, decim=decim, rf_scale=case.rf_scale)
+        if timed: ev[1].record(stream)
+        wf.das_iq(iq, pr, gr, "pwi", decim=decim, f0=f0, angles=case.angles, t_start=case.t_starts,
+                  out=img, workspace=ws)
+        if timed: ev[2].record(stream)
+        wf.iq_envelope(img, out=env, frame_max=fmax)
+        if timed: ev[3].record(stream)
+        wf.logclip(env, ref=fmax, out=db)
+        if timed: ev[4].record(stream)
+
+    for i in range(max(3, args.warmup)):
+        step(i)
+    torch.cuda.synchronize(dev)
+    if args.profile_only:
+        for i in range(args.steps):
+            step(i)
+        torch.cuda.synchronize(dev)
+        return None
+    steps = min(args.steps, 400)
+    with ClockSampler(0) as clk:
+        w0 = time.time()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(steps):
+            step(i)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        clk.region(w0, time.time())
+    ms = e0.elapsed_time(e1) / steps
+    names = ["iq_demod", "das_iq", "iq_envelope", "logclip"]
+    acc = dict.fromkeys(names, 0.0)
+    k = 20
+    for i in range(k):
+        step(i, timed=True)
+        torch.cuda.synchronize(dev)
+        for j, nm in enumerate(names):
+            acc[nm] += ev[j].elapsed_time(ev[j + 1]) / k
+    _, active, contributing, _ = delay_sum_counts(case, dev)
+    return {
+        "metric": "IQ-path B-mode frames/s (demodulation + complex DAS + |IQ| + log-clip per frame)",
+        "value": round(1e3 / ms, 2), "unit": "frames/s", "n_gpus": 1, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"pwi_full_iq: {WORKLOAD_TEXT['pwi_full_iq']}", "frames_per_step": 1,
+                   "l2": "inputs larger than L2: 6 rotating RF copies (384 MiB)",
+                   "launch": "eager library calls"},
+        "stages_ms": {nm: round(v, 4) for nm, v in acc.items()},
+        "g_delay_sums_per_s": {"das_iq_aperture_active": round(active / (acc["das_iq"] / 1e3) / 1e9, 2)},
+        "delay_sums_per_frame": {"aperture_active": active, "contributing_rf": contributing},
+        "gpu_launches": 5 * steps,
+        "clocks": clk.summary(),
+    }
+
+
 # ----------------------------------------------------------------------------- reference arm
 
 def run_reference(args):
@@ -977,9 +1062,9 @@ def main():
         if rank == 0:
             print(json.dumps(run_served(args)), flush=True)
         return
-    if args.workload == "diff_pwi":
+    if args.workload in ("diff_pwi", "pwi_full_iq"):
         if rank == 0:
-            line = run_diff(args)
+            line = run_diff(args) if args.workload == "diff_pwi" else run_iq(args)
             if line is not None:
                 print(json.dumps(line), flush=True)
         return

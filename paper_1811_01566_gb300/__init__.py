@@ -249,6 +249,17 @@ def das_plan(probe: Probe, grid: Grid, mode: str, *, n_tx: int, n_samples: int,
     return {n: getattr(info, n) for n, _ in _WfPlanInfo._fields_}
 
 
+def das_iq_workspace_bytes(probe: Probe, grid: Grid, mode: str, *, batch: int, n_tx: int, m: int,
+                           decim: int) -> int:
+    """Workspace bytes das_iq needs for batch x n_tx traces of m baseband samples (decimation decim)."""
+    n = _load().wf_das_iq_workspace_bytes(C.byref(probe._c()), C.byref(grid._c()),
+                                          {"stai": 0, "pwi": 1}[mode], int(batch), int(n_tx), int(m),
+                                          int(decim))
+    if n == 0:
+        raise WfError(2, "wf_das_iq_workspace_bytes")
+    return int(n)
+
+
 def das_iq(iq: torch.Tensor, probe: Probe, grid: Grid, mode: str, *, decim: int, f0: float,
            tx_elem=None, t_start=None, angles=None, out: torch.Tensor | None = None,
            workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:

@@ -1055,9 +1055,9 @@ extern "C" size_t wf_das_iq_workspace_bytes(const wf_probe* probe, const wf_grid
     thread_local DasArgs A;
     if ((mode != 0 && mode != 1) || n_tx < 1 || n_tx > WF_MAX_TX) return 0;
     std::vector<double> ang(n_tx, 0.0);
-    const double t0 = 0.0;
+    const double t0 = 0.0;   // STAI: one start time; plane waves: NULL, every angle at 0
     size_t need = 0;
-    if (das_iq_prepare(mode, probe, grid, batch, n_tx, nullptr, ang.data(), &t0,
+    if (das_iq_prepare(mode, probe, grid, batch, n_tx, nullptr, ang.data(), mode == 0 ? &t0 : nullptr,
                        probe ? probe->n_elements : 0, m_samples, decim, 0.0, A, need) != WF_OK)
         return 0;
     return need;

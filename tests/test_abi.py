@@ -135,3 +135,17 @@ def test_envelope_and_logclip_argument_checks():
     assert lib.wf_logclip(p, 1, 4, 4, None, 0.0, -1.0, q, None) == 1   # db_min > db_max
     assert lib.wf_logclip(None, 1, 4, 4, None, -60.0, 0.0, q, None) == 1
     assert lib.wf_logclip(p, 0, 4, 4, None, -60.0, 0.0, q, None) == 1
+
+
+@pytest.mark.parametrize("mode", ["stai", "pwi"])
+def test_iq_workspace_query_for_every_transmit_count(mode):
+    """Host-only size query of the IQ DAS, up to the transmit limit.  For plane waves the
+    query plans with every angle starting at 0; it once read a per-angle start-time array
+    that was a single value, which failed for large angle counts."""
+    pr = wf.Probe(128, 0.3e-3, 50e6, 1540.0, 1.5)
+    gr = wf.Grid(1024, 512, -19.05e-3, 19.05e-3, 5e-3, 45e-3)
+    sizes = {n: wf.das_iq_workspace_bytes(pr, gr, mode, batch=1, n_tx=n, m=1024, decim=4)
+             for n in (1, 3, 64, 128)}
+    assert all(v > 0 for v in sizes.values()), sizes
+    # fewer chunk groups per tile when more frames fill the GPU: no more than proportional
+    assert sizes[64] <= wf.das_iq_workspace_bytes(pr, gr, mode, batch=2, n_tx=64, m=1024, decim=4) <= 2 * sizes[64]
