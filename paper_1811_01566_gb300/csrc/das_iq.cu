@@ -31,9 +31,20 @@ __host__ __device__ inline IqSmem iq_smem_layout(int W, int n_elements) {
     off += (size_t)kTableStages * sizeof(Stage);
     L.elems = off;
     off += (((size_t)n_elements * sizeof(Elem)) + 15) & ~(size_t)15;
+    L.raw = off;   // [kC][W + 8] complex samples of the next stage, copied during this one
+    off += (size_t)kC * (W + 8) * sizeof(float2);
     L.total = off;
     return L;
 }
+
+// 8-byte asynchronous copy global -> shared; src_bytes 0 writes zeros without reading.
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc, unsigned src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(smem_dst)), "l"(gsrc),
+                 "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 template <int MODE>
 __global__ void __launch_bounds__(kThreads, 2) das_iq_kernel(const __grid_constant__ DasArgs a) {
@@ -45,6 +56,7 @@ __global__ void __launch_bounds__(kThreads, 2) das_iq_kernel(const __grid_consta
     float2* rot = reinterpret_cast<float2*>(smem_raw + L.rot);     // [W + 8] e^{2 pi i k n}
     Stage* st = reinterpret_cast<Stage*>(smem_raw + L.table);
     Elem* el = reinterpret_cast<Elem*>(smem_raw + L.elems);
+    float2* raw = reinterpret_cast<float2*>(smem_raw + L.raw);      // [kC][W + 8] complex samples
     __shared__ int s_tlist[WF_MAX_TX];
     __shared__ int s_info[4];
     __shared__ int s_cnt[kTableBatch / 32];
@@ -98,6 +110,23 @@ __global__ void __launch_bounds__(kThreads, 2) das_iq_kernel(const __grid_consta
         }
     };
     need(0);
+    // Samples lo .. lo + len of the chunk's rows of entry qq into `raw` by asynchronous copies
+    // (row c = warp, positions 32 apart per lane; zeros outside the record and the chunk),
+    // issued one stage ahead so the global latency runs under the previous stage's work.
+    auto issue_raw = [&](int qq) {
+        const Stage s = st[qq & (kTableStages - 1)];
+        const int rr0 = er.x + s.k() * kC, rlast = min(rr0 + kC - 1, er.y);
+        const bool row_on = rr0 + warp <= rlast;
+        const float2* tr = iq + ((long long)stage_tx<false>(sp, s.j()) * E + rr0 + (row_on ? warp : 0)) * a.ns;
+        float2* dst = raw + warp * (a.W + 8);
+        for (int i = lane; i <= s.len; i += 32) {
+            const int n = s.lo + i;
+            const bool in = row_on && n >= 0 && n < a.ns;
+            cp_async8(dst + i, tr + (in ? n : 0), in ? 8u : 0u);
+        }
+        cp_async_commit();
+    };
+    if (n_live > 0) issue_raw(0);
 
     float acc_re[P], acc_im[P];
 #pragma unroll
@@ -120,7 +149,8 @@ __global__ void __launch_bounds__(kThreads, 2) das_iq_kernel(const __grid_consta
             sincospif(2.0f * fr, &sn, &cs);
             rot[i] = make_float2(cs, sn);
         }
-        __syncthreads();
+        cp_async_wait_all();   // this thread's copies of stage q
+        __syncthreads();       // every copy of stage q and the rotations visible
         // staged pairs (y, d) of the chunk's rows; zero where n or n + 1 is outside the record
         const int len = si.len;
 #pragma unroll 1
@@ -129,16 +159,16 @@ __global__ void __launch_bounds__(kThreads, 2) das_iq_kernel(const __grid_consta
                 const int n = si.lo + i;
                 float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
                 if (r0 + c <= r_last && n >= 0 && n + 1 <= a.ns - 1) {
-                    const float2* tr = iq + ((long long)t * E + r0 + c) * a.ns + n;
-                    const float2 x0 = __ldg(tr), x1 = __ldg(tr + 1), e = rot[i];
+                    const float2 x0 = raw[c * (a.W + 8) + i], x1 = raw[c * (a.W + 8) + i + 1], e = rot[i];
                     const float yr = x0.x * e.x - x0.y * e.y, yi = x0.x * e.y + x0.y * e.x;
                     const float zr = x1.x * e.x - x1.y * e.y, zi = x1.x * e.y + x1.y * e.x;
                     v = make_float4(yr, yi, zr - yr, zi - yi);
                 }
                 buf[c * a.W + i] = v;
             }
-        __syncthreads();
+        __syncthreads();   // pairs visible; raw free
         need(q + 1);
+        if (q + 1 < n_live) issue_raw(q + 1);
         if (k != k_cur) {
             k_cur = k;
             cmask = 0u;

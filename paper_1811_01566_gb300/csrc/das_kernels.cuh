@@ -1276,7 +1276,7 @@ wf_status launch_das_backward(DasArgs& A, const Plan& P, int batch, bool need_rf
 // Delay-and-sum of IQ data (das_iq.cu): shared-memory layout, launch (tiled kernel and
 // the group reduction into the complex image out [batch][nz][nx][2]) and |B| with frame maxima.
 struct IqSmem {
-    size_t pairs, rot, table, elems, total;
+    size_t pairs, rot, table, elems, raw, total;
 };
 size_t iq_smem_bytes(int W, int n_elements);
 template <int MODE>
