@@ -401,6 +401,31 @@ def run_workload(name, args, rank, world, local_rank, *, with_e2e=True, with_clo
     ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
     clocks = clk.summary()
 
+    # ---- per-step distribution (after the timed region): an event between consecutive
+    # steps, the RF buffers still rotating (each step's RF comes from HBM)
+    n_dist = 200
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(n_dist + 1)]
+    barrier()
+    evs[0].record(stream)
+    for i in range(n_dist):
+        run_steps(1, i)
+        evs[i + 1].record(stream)
+    evs[-1].synchronize()
+    per_step = sorted(evs[i].elapsed_time(evs[i + 1]) for i in range(n_dist))
+    # warm: one RF buffer over and over (its 64 MiB stay in the 129 MB L2)
+    evs[0].record(stream)
+    for i in range(n_dist):
+        run_steps(1, 0)
+        evs[i + 1].record(stream)
+    evs[-1].synchronize()
+    warm = sorted(evs[i].elapsed_time(evs[i + 1]) for i in range(n_dist))
+    step_dist = {"n": n_dist, "p50_ms": round(per_step[n_dist // 2], 5),
+                 "p90_ms": round(per_step[(9 * n_dist) // 10], 5), "min_ms": round(per_step[0], 5),
+                 "max_ms": round(per_step[-1], 5),
+                 "warm_p50_ms": round(warm[n_dist // 2], 5), "warm_p90_ms": round(warm[(9 * n_dist) // 10], 5),
+                 "basis": "CUDA events between consecutive steps, outside the timed region; cold = "
+                          "rotating RF buffers (as timed), warm = one buffer repeated"}
+
     # ---- stages alone: graphs holding only the DAS call (memset, tiled kernel, split
     # reduction), only the envelope, only the log-clip, replayed between device events.
     das_graphs = [_graph(lambda i=i: das_call(i)) for i in range(n_bufs)]
@@ -465,6 +490,7 @@ def run_workload(name, args, rank, world, local_rank, *, with_e2e=True, with_clo
                   f"({n_bufs * rf_bytes / 2**20:.0f} MiB > 129 MB L2)",
             "launch": "CUDA graph per step" if graphs is not None else "eager launches",
         },
+        "step_distribution": step_dist,
         "sustained": {"value": round(replica_throughput(b, sus_steps, 1, sus_ms), 2),
                       "unit": "frames/s", "steps": sus_steps, "seconds": round(sus_ms / 1e3, 3),
                       "note": "the same graph-replayed steps over the 0.6 s after the timed ones"},
