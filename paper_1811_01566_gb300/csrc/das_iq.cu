@@ -126,7 +126,21 @@ __global__ void __launch_bounds__(kThreads, 2) das_iq_kernel(const __grid_consta
         }
         cp_async_commit();
     };
-    if (n_live > 0) issue_raw(0);
+    // Rotation e^{2 pi i k n} of the window positions n = lo + i, i = 0 .. len, of a stage.
+    auto make_rot = [&](const Stage& s) {
+        // position lane * 8 + warp: a window of a few dozen positions spreads over all warps
+        for (int i = lane * (kThreads / 32) + warp; i <= s.len; i += kThreads) {
+            const DF ph = df_mul(a.iq_k, DF{(float)(s.lo + i), 0.0f});   // cycles, |lo + i| < 2^22
+            const float fr = (ph.hi - rintf(ph.hi)) + ph.lo;
+            float sn, cs;
+            sincospif(2.0f * fr, &sn, &cs);
+            rot[i] = make_float2(cs, sn);
+        }
+    };
+    if (n_live > 0) {
+        issue_raw(0);
+        make_rot(st[0]);
+    }
 
     float acc_re[P], acc_im[P];
 #pragma unroll
@@ -141,21 +155,16 @@ __global__ void __launch_bounds__(kThreads, 2) das_iq_kernel(const __grid_consta
         const int r0 = er.x + k * kC;
         const int r_last = min(r0 + kC - 1, er.y);
         const int t = stage_tx<false>(sp, si.j());
-        // rotation e^{2 pi i k n} of the window positions n = lo + i, i = 0 .. len
-        for (int i = tid; i <= si.len; i += kThreads) {
-            const DF ph = df_mul(a.iq_k, DF{(float)(si.lo + i), 0.0f});   // cycles, |lo + i| < 2^22
-            const float fr = (ph.hi - rintf(ph.hi)) + ph.lo;
-            float sn, cs;
-            sincospif(2.0f * fr, &sn, &cs);
-            rot[i] = make_float2(cs, sn);
-        }
         cp_async_wait_all();   // this thread's copies of stage q
-        __syncthreads();       // every copy of stage q and the rotations visible
+        // every copy and the rotations of stage q visible; every warp done with stage q - 1's
+        // pairs (its compute precedes this barrier), so they may be overwritten
+        __syncthreads();
         // staged pairs (y, d) of the chunk's rows; zero where n or n + 1 is outside the record
         const int len = si.len;
-#pragma unroll 1
-        for (int c = 0; c < kC; ++c)   // row by row: no division by the run-time window length
-            for (int i = tid; i < len; i += kThreads) {
+        {
+            static_assert(kThreads / 32 == kC, "one trace row per warp");
+            const int c = warp;   // one trace row per warp, lanes along the window: equal shares
+            for (int i = lane; i < len; i += 32) {
                 const int n = si.lo + i;
                 float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
                 if (r0 + c <= r_last && n >= 0 && n + 1 <= a.ns - 1) {
@@ -166,9 +175,13 @@ __global__ void __launch_bounds__(kThreads, 2) das_iq_kernel(const __grid_consta
                 }
                 buf[c * a.W + i] = v;
             }
-        __syncthreads();   // pairs visible; raw free
+        }
+        __syncthreads();   // pairs visible; raw and the rotation table free
         need(q + 1);
-        if (q + 1 < n_live) issue_raw(q + 1);
+        if (q + 1 < n_live) {   // stage q + 1's samples and rotations, under stage q's compute
+            issue_raw(q + 1);
+            make_rot(st[(q + 1) & (kTableStages - 1)]);
+        }
         if (k != k_cur) {
             k_cur = k;
             cmask = 0u;
@@ -252,7 +265,6 @@ __global__ void __launch_bounds__(kThreads, 2) das_iq_kernel(const __grid_consta
                 acc_im[p] = fmaf(wt[p], si_[p], acc_im[p]);
             }
         }
-        __syncthreads();   // pairs and rotations of stage q no longer read
     }
     float2* dst = reinterpret_cast<float2*>(a.part) + ((long long)b * a.n_items + item) * (kThreads * P);
 #pragma unroll
