@@ -106,3 +106,25 @@ def test_iq_das_rejects_bad_arguments():
         wf.das_iq(iq, pr, gr, "pwi", decim=0, f0=F0, angles=case.angles)
     with pytest.raises(ValueError):
         wf.das_iq(iq.real.contiguous(), pr, gr, "pwi", decim=1, f0=F0, angles=case.angles)
+
+
+def test_iq_full_pwi_frame_row_bands_match_oracle():
+    """The full plane-wave frame through the IQ path as bench.py times it (int16 RF
+    demodulated at 5 MHz with a 63-tap low-pass and decimation 4, complex DAS on the
+    1024 x 512 grid): three bands of rows (top, middle, bottom) against the oracle run on
+    the same baseband traces."""
+    case = configs.pwi_full(device="cuda", dtype="i16")
+    pr, gr = probe_grid(case)
+    n = np.arange(63) - 31
+    cut = 3e6 / case.fs
+    taps = (2 * cut * np.sinc(2 * cut * n) * np.hamming(63)).astype(np.float32)
+    iq = wf.iq_demod(torch.from_numpy(case.rf).cuda(), F0, case.fs, taps, decim=4, rf_scale=case.rf_scale)
+    img = wf.das_iq(iq, pr, gr, "pwi", decim=4, f0=F0, angles=case.angles,
+                    t_start=case.t_starts)[0].cpu().numpy()
+    iq_h = iq[0].cpu().numpy().astype(np.complex128)
+    opr, ogr = oracle.probe_grid(case)
+    for r0, r1 in ((0, 32), (480, 544), (992, 1024)):
+        want = oracle.das_iq(iq_h, opr, ogr, mode="pwi", decim=4, f0=F0, angles=case.angles,
+                             t_starts=case.t_starts, rows=(r0, r1), threads=THREADS)[r0:r1]
+        err = rel_l2(img[r0:r1], want)
+        assert err <= TOL_BF_REL_L2, (r0, r1, err)
