@@ -104,11 +104,19 @@ template <typename T>
 __global__ void __launch_bounds__(kIqThreads) iq_kernel(const __grid_constant__ FirArgs a,
                                                         const T* __restrict__ x, float2* __restrict__ iq,
                                                         int n_out) {
-    extern __shared__ __align__(16) float2 xm[];         // mixed input span
+    // The mixed input span, stored by decimation phase: xm[p * plen + jj] = span sample
+    // jj D + p.  Output t of the block sums taps u = v D + p over phase p at position t + v,
+    // so adjacent threads read adjacent words (a plain span read at stride D conflicts on the
+    // shared-memory banks for every D > 1).
+    extern __shared__ __align__(16) float2 xm[];
     const int c = (a.n_taps - 1) / 2;
+    const int D = a.decim;
     const int m0 = blockIdx.x * kIqThreads;
-    const int i0 = m0 * a.decim + c - (a.n_taps - 1);    // first input index of the span
-    const int span = (kIqThreads - 1) * a.decim + a.n_taps;
+    const int i0 = m0 * D + c - (a.n_taps - 1);          // first input index of the span
+    const int span = (kIqThreads - 1) * D + a.n_taps;
+    const int plen = (span + D - 1) / D;                 // span samples per phase
+    // j / D = (j * ceil(2^20 / D)) >> 20, exact for D <= 16 and j < 4400 (span <= 4335)
+    const unsigned mdiv = ((1u << 20) + (unsigned)D - 1u) / (unsigned)D;
     for (long long tr = blockIdx.y; tr < a.n_traces; tr += gridDim.y) {
         const T* src = x + tr * a.ns;
         for (int j = threadIdx.x; j < span; j += kIqThreads) {
@@ -120,19 +128,23 @@ __global__ void __launch_bounds__(kIqThreads) iq_kernel(const __grid_constant__ 
                 sincospif(2.0f * mix_turns(a.turns, i), &sn, &cs);
                 v = make_float2(s * cs, -s * sn);
             }
-            xm[j] = v;
+            const int jj = (int)(((unsigned)j * mdiv) >> 20);
+            xm[(j - jj * D) * plen + jj] = v;
         }
         __syncthreads();
         const int m = m0 + threadIdx.x;
         if (m < n_out) {
-            // iq[m] = sum_k h[k] xm[m D + c - k - i0] = sum_u hr[u] xm[t D + u], t = m - m0
-            const float2* w = xm + threadIdx.x * a.decim;
+            // iq[m] = sum_k h[k] x[m D + c - k] = sum_u hr[u] span[t D + u], t = m - m0; with
+            // u = v D + p that is phase p at position t + v
             float re = 0.0f, im = 0.0f;
-            for (int u = 0; u < a.n_taps; ++u) {
-                const float h = a.hr[u];
-                const float2 v = w[u];
-                re = fmaf(h, v.x, re);
-                im = fmaf(h, v.y, im);
+            for (int p = 0; p < D && p < a.n_taps; ++p) {
+                const float2* w = xm + p * plen + threadIdx.x;
+                for (int u = p, v = 0; u < a.n_taps; u += D, ++v) {
+                    const float h = a.hr[u];
+                    const float2 x2 = w[v];
+                    re = fmaf(h, x2.x, re);
+                    im = fmaf(h, x2.y, im);
+                }
             }
             iq[tr * n_out + m] = make_float2(re, im);
         }
@@ -199,7 +211,7 @@ extern "C" wf_status wf_iq_demod(const void* rf, wf_dtype dtype, float rf_scale,
     if (r < 0.0) r += 1.0;
     a.turns = df_from_double(r);
     const int n_out = (n_samples + decim - 1) / decim;
-    const size_t smem = sizeof(float2) * ((kIqThreads - 1) * (size_t)decim + n_taps);
+    const size_t smem = sizeof(float2) * ((kIqThreads - 1) * (size_t)decim + n_taps + decim);   // phases padded
     dim3 grid((n_out + kIqThreads - 1) / kIqThreads, (unsigned)std::min<int64_t>(n_traces, 65535));
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     float2* o = reinterpret_cast<float2*>(out_iq);
