@@ -16,7 +16,7 @@
 // the formulation of Govindaraju et al., "High performance discrete Fourier
 // transforms on graphics processors", SC 2008); twiddles from sincospif of
 // exact arguments 2m/N; the epilogue fuses the magnitude and the per-frame
-// maximum.  The reverse kernel keeps one column pair per CTA and radix-2 passes.
+// maximum.  The reverse kernel takes one column pair per CTA with the same passes.
 #include <algorithm>
 #include <cmath>
 
@@ -228,13 +228,14 @@ __global__ void __launch_bounds__(kEnvThreads) envelope_backward_kernel(
     float2* A = reinterpret_cast<float2*>(smem_raw);     // [PAIRS][n]
     float2* B = A + PAIRS * n;                            // [PAIRS][n]
     float2* R = B + PAIRS * n;                            // [PAIRS][n] real parts of g
-    float2* tw = R + PAIRS * n;                           // [n/2]
+    float2* tw = R + PAIRS * n;                           // [3n/4] (n/2 for n = 2)
     const int b = blockIdx.y;
     const int x0 = blockIdx.x * (2 * PAIRS);
     const long long fo = (long long)b * nz * nx;
     const float* src = bf + fo;
 
-    for (int m = threadIdx.x; m < (n >> 1); m += blockDim.x) {
+    const int ntw = n >= 4 ? 3 * (n >> 2) : (n >> 1);
+    for (int m = threadIdx.x; m < ntw; m += blockDim.x) {
         float s, c;
         sincospif(2.0f * (float)m / (float)n, &s, &c);
         tw[m] = make_float2(c, -s);
@@ -250,27 +251,19 @@ __global__ void __launch_bounds__(kEnvThreads) envelope_backward_kernel(
     // Paired Hilbert transform of the sequences in `buf` (result n * (h_a + i h_b) in the
     // returned buffer).
     auto hilbert = [&](float2* in, float2* out) {
-        for (int ns = 1; ns < n; ns <<= 1) {
-            stockham_pass(in, out, tw, n, log2n, ns, PAIRS, false);
-            __syncthreads();
-            float2* t = in; in = out; out = t;
-        }
+        float2* y = stockham_fft(in, out, tw, n, log2n, PAIRS, false);
+        float2* o = y == in ? out : in;
         for (int q = threadIdx.x; q < PAIRS * n; q += blockDim.x) {
             const int k = q & (n - 1);
-            const float2 y = in[q];
+            const float2 v = y[q];
             float2 gv;
             if (k == 0 || 2 * k == n) gv = make_float2(0.0f, 0.0f);
-            else if (2 * k < n) gv = make_float2(y.y, -y.x);
-            else gv = make_float2(-y.y, y.x);
-            in[q] = gv;
+            else if (2 * k < n) gv = make_float2(v.y, -v.x);
+            else gv = make_float2(-v.y, v.x);
+            y[q] = gv;
         }
         __syncthreads();
-        for (int ns = 1; ns < n; ns <<= 1) {
-            stockham_pass(in, out, tw, n, log2n, ns, PAIRS, true);
-            __syncthreads();
-            float2* t = in; in = out; out = t;
-        }
-        return in;
+        return stockham_fft(y, o, tw, n, log2n, PAIRS, true);
     };
     float2* h = hilbert(A, B);
     float2* other = h == A ? B : A;
@@ -382,9 +375,9 @@ extern "C" wf_status wf_envelope_backward(const float* bf, int32_t batch, int32_
     while ((1 << log2n) < nz) ++log2n;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     constexpr int kPairs = 1;
-    const size_t smem = sizeof(float2) * (3 * kPairs * (size_t)nz + nz / 2);
+    const size_t smem = sizeof(float2) * (3 * kPairs * (size_t)nz + (nz >= 4 ? 3 * (nz / 4) : nz / 2));
     static unsigned long long smem_set = 0ull;
-    const size_t smem_max = sizeof(float2) * (3 * kPairs * 4096 + 2048);
+    const size_t smem_max = sizeof(float2) * (3 * kPairs * 4096 + 3 * 1024);
     wf_status s = ensure_smem_limit(envelope_backward_kernel<kPairs>, smem_max, smem_set);
     if (s != WF_OK) return s;
     dim3 grid((nx + 2 * kPairs - 1) / (2 * kPairs), batch);
