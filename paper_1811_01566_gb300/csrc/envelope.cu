@@ -333,11 +333,12 @@ wf_status envelope_forward(const float* bf, int32_t batch, int32_t nz, int32_t n
     }
     // Column pairs per CTA: as many as keep at least ~600 CTAs in flight (four SM-fulls of
     // 152 SMs), up to four (eight adjacent columns: one 32-byte sector per row), two at
-    // nz = 4096 (shared memory); one thread per radix-4 butterfly of a pass.
+    // nz = 4096 (shared memory); one thread per radix-4 butterfly of a pass, at least 256
+    // threads (the loads and the epilogue run on all of them).
     const long long col_pairs = (long long)batch * ((nx + 1) / 2);
     int pairs = 1;
     while (pairs < (nz <= 2048 ? 4 : 2) && col_pairs / (2 * pairs) >= 600) pairs *= 2;
-    const int threads = (int)std::min<long long>(kEnvFwdThreads, std::max<long long>(64, (long long)pairs * nz / 4));
+    const int threads = (int)std::min<long long>(kEnvFwdThreads, std::max<long long>(256, (long long)pairs * nz / 4));
     const size_t smem = sizeof(float2) * (2 * (size_t)pairs * nz + (nz >= 4 ? 3 * (nz / 4) : nz / 2));
     static unsigned long long smem_set = 0ull;
     const size_t smem_max = sizeof(float2) * (2 * 2 * 4096 + 3 * 1024);
